@@ -1,0 +1,83 @@
+"""Pins of the ground-state flow (eq. groundDef on S_M).
+
+- Lemma SMA (FM, beta_s < 0, beta_n + beta_s >= 0, p = q = 0): Phi = a phi_g with
+  a = ((1+M)/2, ((1-M^2)/2)^{1/2}, (1-M)/2), equal chemical potentials, and
+  phi_g solving the scalar equation with interaction beta_n + beta_s.
+- Lemma on the two-component AFM state (beta_s > 0, M != 0): phi_0 = 0.
+- Non-interacting limit: the oscillator ground state, mu_j = sum gamma / 2.
+- Constraints: mass 1 and magnetization M; NLEP residual <= 1e-12.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import discretization as disc
+from oracle import ground_state as gs
+from oracle import spin1
+
+
+def _run(w):
+    V = synth.potential(w)
+    phi, mu, res, it = gs.ground_state(w, V, synth.initial_spinor(w), tol=1e-12)
+    return V, phi, mu, res
+
+
+@pytest.mark.parametrize("M", [0.0, 0.3])
+def test_sma_ferromagnetic(M):
+    w = synth.Workload("sma", (128,), (-16.0,), (16.0,), (1.0,), 10.0, -1.0, 0.0, 0.0, M=M, gs_seed=5)
+    V, phi, mu, res = _run(w)
+    assert res <= 1e-12
+    a = np.array([(1 + M) / 2, np.sqrt((1 - M * M) / 2), (1 - M) / 2])
+    # the sign of a global spin rotation is free: compare |phi|
+    ratios = np.abs(phi) / np.abs(phi[1])[None]
+    core = np.abs(phi[1]) > 1e-3 * np.abs(phi[1]).max()
+    for j in range(3):
+        assert np.allclose(ratios[j][core], a[j] / a[1], rtol=1e-9)
+    assert np.ptp(mu) < 1e-10
+    phig = phi[1] * np.sign(phi[1][np.argmax(np.abs(phi[1]))]) / a[1]
+    lap = disc.laplacian_fft(phig, w.lo, w.hi).real
+    r = -0.5 * lap + (V + (w.beta_n + w.beta_s) * phig ** 2) * phig - mu[1] * phig
+    assert np.abs(r).max() < 1e-10
+
+
+def test_constraints_and_residual():
+    w = synth.Workload("c", (64, 64), (-8.0, -8.0), (8.0, 8.0), (1.0, 1.2), 40.0, -1.0, 0.0, 0.1,
+                       M=0.2, gs_seed=9)
+    V, phi, mu, res = _run(w)
+    cell = float(np.prod(w.h))
+    assert res <= 1e-12
+    assert abs(cell * np.sum(phi ** 2) - 1) < 1e-12
+    assert abs(cell * (np.sum(phi[0] ** 2) - np.sum(phi[2] ** 2)) - 0.2) < 1e-12
+    assert abs(mu[0] + mu[2] - 2 * mu[1]) < 1e-10
+
+
+def test_antiferromagnetic_two_component():
+    w = synth.Workload("afm", (128,), (-12.0,), (12.0,), (1.0,), 30.0, 2.0, 0.0, 0.0, M=0.3, gs_seed=3)
+    V, phi, mu, res = _run(w)
+    assert res <= 1e-12
+    cell = w.h[0]
+    assert cell * np.sum(phi[1] ** 2) < 1e-16
+
+
+def test_non_interacting_oscillator():
+    w = synth.Workload("free", (64, 32), (-8.0, -6.0), (8.0, 6.0), (1.0, 2.0), 0.0, 0.0, M=0.0, gs_seed=4)
+    V, phi, mu, res = _run(w)
+    assert res <= 1e-12
+    assert np.allclose(mu, 1.5, atol=1e-11)
+    x, y = np.meshgrid(*synth.axes(w), indexing="ij")
+    g = np.exp(-(1.0 * x * x + 2.0 * y * y) / 2)
+    for j in range(3):
+        c = np.sum(phi[j] * g) / np.sum(g * g)
+        assert np.abs(phi[j] - c * g).max() < 1e-9
+
+
+def test_chemical_potential_rules():
+    phi = np.zeros((3, 4))
+    phi[1] = 1.0
+    Hphi = 2.5 * phi
+    mu = spin1.chemical_potentials(phi, Hphi)
+    assert np.allclose(mu, 2.5)
+    phi = np.ones((3, 4))
+    phi[1] = 0.0
+    Hphi = np.stack([1.0 * phi[0], 0 * phi[1], 3.0 * phi[2]])
+    assert np.allclose(spin1.chemical_potentials(phi, Hphi), [1.0, 2.0, 3.0])

@@ -1,0 +1,191 @@
+"""Pins of the linear-response eigenproblem (Sections 2.2-2.3, 3.1-3.2).
+
+- Theorem "Symmetric distribution": the dense UV spectrum comes in +-omega pairs.
+- Two independent dense routes (scipy.linalg.eig on eq. BdG-d; Cholesky-eigh
+  on eq. lrep-d) give the same positive spectrum.
+- Theorems on the generalized nullspace (FM, Lemma SMA): four zero modes,
+  null(H_-) = span{Phi_1, Phi_2}, null(H_+) = span{Phi_2}, a Jordan partner
+  H_+ Phi^_1 = Phi_1 with <Phi^_1, Phi_1> > 0; AFM conjecture: four zero modes.
+- Theorem "Analytical eigenpairs": omega = gamma_alpha with the closed-form
+  (u, v) from d_alpha Phi and x_alpha Phi.
+- Non-interacting limit: omega = n gamma, each level three-fold (spin).
+- Theorem "Biorthogonality" / eq. constrainfg: h^d (u_i.u_j - v_i.v_j) = delta_ij.
+- biortho and small_lrep against their defining properties and scipy.
+- The iterative solver against the dense route.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import synth
+from oracle import apply as ap
+from oracle import kohn, lrep
+
+from conftest import relerr
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+WFM = synth.Workload("fm1d", (128,), (-16.0,), (16.0,), (1.0,), 10.0, -1.0, 0.0, 0.0, gs_seed=101)
+WAFM = synth.Workload("afm1d", (128,), (-12.0,), (12.0,), (1.0,), 30.0, 2.0, 0.0, 0.0, M=0.3, gs_seed=3)
+WQ = synth.Workload("q2d", (16, 16), (-6.0, -6.0), (6.0, 6.0), (1.0, 1.4), 12.0, -1.0, 0.05, 0.3, gs_seed=8)
+
+
+def _op(ground, w):
+    V, phi, mu = ground(w)
+    return ap.Operator(w, phi, V, mu), phi
+
+
+@pytest.mark.parametrize("w", [WFM, WQ])
+def test_pm_pairing_and_two_dense_routes(ground, w):
+    op, _ = _op(ground, w)
+    ev = lrep.dense_eig_uv(op)
+    # away from the (Jordan) zero modes the spectrum is real
+    assert np.abs(ev.imag[np.abs(ev) > 1e-5]).max() < 1e-8
+    re = np.sort(ev.real)
+    assert np.allclose(np.sort(re[re > 1e-5]), np.sort(-re[re < -1e-5]), atol=1e-9)
+    pos = np.sort(re[re > 1e-5])[:12]
+    om, F, G = lrep.dense_solve_fg(op, 12)
+    assert np.allclose(om, pos, rtol=1e-10)
+
+
+def test_fm_generalized_nullspace(ground):
+    op, phi = _op(ground, WFM)
+    ev = lrep.dense_eig_uv(op)
+    assert np.sum(np.abs(ev) < 1e-5) == 4
+    P = op.npts
+    phig = phi[1] / np.sqrt(0.5)
+    a = np.array([0.5, np.sqrt(0.5), 0.5])
+    b = np.array([np.sqrt(0.5), 0.0, -np.sqrt(0.5)])
+    Phi1 = (a[:, None] * phig[None]).reshape(1, 3, P)
+    Phi2 = (b[:, None] * phig[None]).reshape(1, 3, P)
+    scale = np.linalg.norm(op.hplus(Phi1))
+    assert np.linalg.norm(op.hminus(Phi1)) < 1e-10 * scale
+    assert np.linalg.norm(op.hminus(Phi2)) < 1e-10 * scale
+    assert np.linalg.norm(op.hplus(Phi2)) < 1e-10 * scale
+    A, B = op.dense_blocks()
+    hat, *_ = np.linalg.lstsq(A + B, Phi1.ravel(), rcond=None)
+    assert np.linalg.norm((A + B) @ hat - Phi1.ravel()) < 1e-9 * np.linalg.norm(Phi1)
+    hat -= Phi2.ravel() * (Phi2.ravel() @ hat) / (Phi2.ravel() @ Phi2.ravel())
+    assert hat @ Phi1.ravel() > 0
+
+
+def test_afm_zero_modes_and_hminus_null(ground):
+    op, phi = _op(ground, WAFM)
+    ev = lrep.dense_eig_uv(op)
+    assert np.sum(np.abs(ev) < 1e-5) == 4
+    M = WAFM.M
+    b1, bm = -np.sqrt((1 - M) / (1 + M)), np.sqrt((1 + M) / (1 - M))
+    Phi2 = np.stack([b1 * phi[0], 0 * phi[1], bm * phi[2]]).reshape(1, 3, -1)
+    assert np.linalg.norm(op.hminus(Phi2)) < 1e-10 * np.linalg.norm(op.hplus(Phi2))
+
+
+def test_kohn_mode(ground):
+    w = synth.Workload("k1d", (256,), (-16.0,), (16.0,), (1.0,), 10.0, -1.0, 0.0, 0.0, gs_seed=101)
+    op, phi = _op(ground, w)
+    om, F, G = lrep.dense_solve_fg(op, 8)
+    i = np.argmin(np.abs(om - 1.0))
+    assert abs(om[i] - 1.0) < 1e-11
+    (gam, f, g), = kohn.kohn_modes(w, phi)
+    assert relerr(op.hplus(f[None])[0], gam * g[None][0]) < 1e-10
+    assert relerr(op.hminus(g[None])[0], gam * f[None][0]) < 1e-10
+    u, v = f + g, f - g
+    U, Vv = (F[i] + G[i]).ravel(), (F[i] - G[i]).ravel()
+    assert kohn.e_uv(U, Vv, u.ravel()[:, None], v.ravel()[:, None]) < 1e-9
+
+
+def test_non_interacting_spectrum(ground):
+    w = synth.Workload("free2d", (28, 20), (-6.5, -4.5), (6.5, 4.5), (1.0, 2.0), 0.0, 0.0, gs_seed=4)
+    op, _ = _op(ground, w)
+    om, F, G = lrep.dense_solve_fg(op, 18)
+    # levels n_x + 2 n_y: 1 (x1), 2 (x2: (2,0),(0,1)), 3 (x2), 4 (x3) ... each x3 in spin
+    expect = np.repeat([1.0, 2.0, 3.0, 4.0], [3, 6, 6, 9])[:18]
+    assert np.allclose(om, expect, atol=1e-10)
+
+
+@pytest.mark.parametrize("w", [WFM, WQ])
+def test_biorthogonality_and_normalization(ground, w):
+    op, _ = _op(ground, w)
+    om, F, G = lrep.dense_solve_fg(op, 10)
+    hd = lrep.weight(w)
+    U = (F + G).reshape(10, -1)
+    V = (F - G).reshape(10, -1)
+    gram = hd * (U @ U.T - V @ V.T)
+    assert np.allclose(gram, np.eye(10), atol=1e-9)
+    # residual of the normalized pairs through the UV operator
+    r = lrep.residual_uv(op, np.concatenate([F + G, F - G], axis=1), om)
+    assert r.max() < 1e-10
+
+
+def test_biortho_properties():
+    rng = np.random.default_rng(0)
+    n, c, l = 200, 7, 3
+    Fl = rng.standard_normal((n, l)) + 1j * rng.standard_normal((n, l))
+    Gl = rng.standard_normal((n, l)) + 1j * rng.standard_normal((n, l))
+    Fl, Gl, _ = lrep.biortho(Fl, Gl)
+    F = rng.standard_normal((n, c)) + 1j * rng.standard_normal((n, c))
+    G = rng.standard_normal((n, c)) + 1j * rng.standard_normal((n, c))
+    F2, G2, r = lrep.biortho(F, G, Fl, Gl)
+    assert r == c
+    assert np.allclose(F2.conj().T @ G2, np.eye(c), atol=1e-12)
+    assert np.abs(Gl.conj().T @ F2).max() < 1e-12 and np.abs(Fl.conj().T @ G2).max() < 1e-12
+    # spans are preserved (modulo the locked block)
+    P = np.linalg.lstsq(np.hstack([F, Fl]), F2, rcond=None)[0]
+    assert np.linalg.norm(np.hstack([F, Fl]) @ P - F2) < 1e-10 * np.linalg.norm(F2)
+    # a duplicated column is a breakdown: the rank drops
+    Fd = np.hstack([F, F[:, :1]])
+    Gd = np.hstack([G, G[:, :1]])
+    _, _, rd = lrep.biortho(Fd, Gd, rtol=1e-10)
+    assert rd == c
+
+
+def test_small_lrep_against_scipy():
+    rng = np.random.default_rng(1)
+    n = 9
+    X = rng.standard_normal((n, n))
+    Kp = X @ X.T + n * np.eye(n)
+    Y = rng.standard_normal((n, n))
+    Km = Y @ Y.T + 0.5 * np.eye(n)
+    om, Pc, Qc = lrep.small_lrep(Kp, Km)
+    big = np.block([[np.zeros((n, n)), Km], [Kp, np.zeros((n, n))]])
+    ev = np.sort(sla.eig(big, right=False).real)
+    assert np.allclose(om, ev[ev > 0], rtol=1e-12)
+    assert np.allclose(Km @ Qc, Pc * om, atol=1e-10) and np.allclose(Kp @ Pc, Qc * om, atol=1e-10)
+    assert np.allclose(Pc.T @ Qc, np.eye(n), atol=1e-10)
+
+
+def test_iterative_solver_matches_dense(ground):
+    w = synth.Workload("it1d", (64,), (-10.0,), (10.0,), (1.0,), 10.0, -1.0, 0.0, 0.0, k=8, m=12,
+                       gs_seed=101, block_seed=7)
+    op, phi = _op(ground, w)
+    Zf, Zg = lrep.deflation_bases(op, phi)
+    X0 = synth.random_block(w, w.m, complex_=False)
+    om, F, G, res, it = lrep.solve_iterative(op, w.k, w.m, X0, Zf, Zg, tol=1e-10, maxit=400)
+    assert res.max() <= 1e-10
+    om_d, Fd, Gd = lrep.dense_solve_fg(op, w.k)
+    assert np.allclose(om, om_d, rtol=1e-10)
+    r = lrep.residual_uv(op, np.concatenate([F + G, F - G], axis=1), om)
+    assert r.max() < 1e-9
+
+
+def test_table1_case1_fm(ground):
+    """Table 1 (Example "Accuracy", Case I, 1D FM, beta_n = 885.4,
+    beta_s = -4.1, L = 16, gamma_x = 1; M not stated, read as 0): the
+    Kohn-mode errors e_omega and e_uv at h0/2 and h0/4 reproduce the printed
+    values (e_omega to 1%, e_uv to 30%: the analytical eigenspace depends on
+    how d_x Phi_g is formed)."""
+    with open(os.path.join(HERE, "golden", "table1_case1_fm.json")) as fh:
+        gold = json.load(fh)
+    for n, key in ((64, "h0/2"), (128, "h0/4")):
+        w = synth.Workload(f"t1_{n}", (n,), (-16.0,), (16.0,), (1.0,), 885.4, -4.1, gs_seed=17)
+        op, phi = _op(ground, w)
+        om, F, G = lrep.dense_solve_fg(op, 40)
+        i = int(np.argmin(np.abs(om - 1.0)))
+        eom = abs(om[i] - 1.0)
+        (gam, f, g), = kohn.kohn_modes(w, phi)
+        euv = kohn.e_uv((F[i] + G[i]).ravel(), (F[i] - G[i]).ravel(),
+                        (f + g).ravel()[:, None], (f - g).ravel()[:, None])
+        pe, pu = gold["e_omega"][key], gold["e_uv"][key]
+        assert abs(eom - pe) < 0.01 * pe, (key, eom, pe)
+        assert abs(euv - pu) < 0.3 * pu, (key, euv, pu)
