@@ -82,7 +82,7 @@ constexpr int UCOLS = 16;
 template <typename R>
 __global__ void __launch_bounds__(256) k_update(PairBlock<R> A, const double* __restrict__ C, int ldc,
                                                 double beta, typename CT<R>::T* __restrict__ Y,
-                                                long long ldy, int Q) {
+                                                long long ldy, int Q, double alpha) {
   typedef typename CT<R>::T T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sC = reinterpret_cast<R*>(smem_raw);  // [2P][UCOLS]
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) k_update(PairBlock<R> A, const double* __
   const int Q2 = 2 * Q;
   for (int e = threadIdx.x; e < P2 * UCOLS; e += blockDim.x) {
     const int k = e / UCOLS, j = e - k * UCOLS;
-    sC[e] = (j0 + j < Q2) ? (R)C[(long long)k * ldc + j0 + j] : (R)0;
+    sC[e] = (j0 + j < Q2) ? (R)(alpha * C[(long long)k * ldc + j0 + j]) : (R)0;
   }
   __syncthreads();
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -179,7 +179,7 @@ cudaError_t gram_pairs(const PairBlock<R>& A, const PairBlock<R>& B, double* G_d
 
 template <typename R>
 cudaError_t update_pairs(const PairBlock<R>& A, const double* C_dev, int ldc, double beta,
-                         typename CT<R>::T* Y, long long ldy, int Q, cudaStream_t s) {
+                         typename CT<R>::T* Y, long long ldy, int Q, cudaStream_t s, double alpha) {
   if (Q <= 0 || A.n == 0) return cudaSuccess;
   if (A.cols == 0) {
     return scale_pairs<R>(Y, ldy, A.n, Q, nullptr, beta, s);
@@ -189,7 +189,7 @@ cudaError_t update_pairs(const PairBlock<R>& A, const double* C_dev, int ldc, do
   cudaError_t e = cudaFuncSetAttribute(k_update<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((A.n + 255) / 256), (unsigned)((2 * Q + UCOLS - 1) / UCOLS));
-  k_update<R><<<grid, 256, sm, s>>>(A, C_dev, ldc, beta, Y, ldy, Q);
+  k_update<R><<<grid, 256, sm, s>>>(A, C_dev, ldc, beta, Y, ldy, Q, alpha);
   return cudaGetLastError();
 }
 
@@ -214,9 +214,9 @@ template cudaError_t gram_pairs<float>(const PairBlock<float>&, const PairBlock<
 template cudaError_t gram_pairs<double>(const PairBlock<double>&, const PairBlock<double>&, double*,
                                         void*, size_t, cudaStream_t);
 template cudaError_t update_pairs<float>(const PairBlock<float>&, const double*, int, double,
-                                         float2*, long long, int, cudaStream_t);
+                                         float2*, long long, int, cudaStream_t, double);
 template cudaError_t update_pairs<double>(const PairBlock<double>&, const double*, int, double,
-                                          double2*, long long, int, cudaStream_t);
+                                          double2*, long long, int, cudaStream_t, double);
 template cudaError_t convert_pairs<double, float>(const double2*, long long, float2*, long long,
                                                   long long, int, cudaStream_t);
 template cudaError_t convert_pairs<float, double>(const float2*, long long, double2*, long long,

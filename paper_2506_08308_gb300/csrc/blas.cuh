@@ -28,12 +28,12 @@ cudaError_t gram_pairs(const PairBlock<R>& A, const PairBlock<R>& B, double* G_d
                        size_t ws_bytes, cudaStream_t s);
 size_t gram_workspace_bytes(int P, int Q, long long n);
 
-// Y[:, q].t = beta * Y[:, q].t + sum_{p,s} A[:, p].s * C[(2p+s) * ldc + 2q+t]
+// Y[:, q].t = beta * Y[:, q].t + alpha * sum_{p,s} A[:, p].s * C[(2p+s) * ldc + 2q+t]
 // C is FP64 on the device (row-major 2P x 2Q with leading dimension ldc);
 // A and Y must not overlap.
 template <typename R>
 cudaError_t update_pairs(const PairBlock<R>& A, const double* C_dev, int ldc, double beta,
-                         typename CT<R>::T* Y, long long ldy, int Q, cudaStream_t s);
+                         typename CT<R>::T* Y, long long ldy, int Q, cudaStream_t s, double alpha = 1.0);
 
 // Y = convert(X) column by column (FP64 <-> FP32 or same type), n complex
 // elements per column, cols columns.

@@ -158,10 +158,10 @@ static bdg_status dot_cols(bdg_plan_t plan, const void* a, const void* b, long l
 // Build the real vectors used at set-up from (phi_1, phi_0, phi_-1, V):
 // kind 0: [0,0,0, phi] (FG vector), 1: Phi, 2: S_z Phi, 3: -i S_y Phi
 // (f-part 3 x N_p complex with zero imaginary parts).
-__global__ void k_build(const double4* __restrict__ pv, long long np, int kind, double2* __restrict__ out) {
+__global__ void k_build(const dquad* __restrict__ pv, long long np, int kind, double2* __restrict__ out) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < np;
        i += (long long)gridDim.x * blockDim.x) {
-    const double4 v = pv[i];
+    const dquad v = pv[i];
     double c0, c1, c2;
     if (kind == 0 || kind == 1) { c0 = v.x; c1 = v.y; c2 = v.z; }
     else if (kind == 2) { c0 = v.x; c1 = 0.0; c2 = -v.z; }
@@ -349,7 +349,7 @@ bdg_status bdg_plan_create(bdg_plan_t* out, const bdg_params* p, const double* V
   memset(&plan->stats, 0, sizeof(plan->stats));
   cudaGetDevice(&plan->device);
   const long long np = g.npts;
-  std::vector<double4> h64(np);
+  std::vector<dquad> h64(np);
   std::vector<float4> h32(np);
   for (long long i = 0; i < np; ++i) {
     const double a = phi[i], b = phi[np + i], c = phi[2 * np + i], v = V[i];
@@ -357,7 +357,7 @@ bdg_status bdg_plan_create(bdg_plan_t* out, const bdg_params* p, const double* V
       free_plan(plan);
       return fail(nullptr, BDG_ERR_NAN, "phi or V holds NaN/Inf");
     }
-    h64[i] = make_double4(a, b, c, v);
+    h64[i] = dquad{a, b, c, v};
     h32[i] = make_float4((float)a, (float)b, (float)c, (float)v);
   }
 #define CREATE_TRY(call)                                                                     \
@@ -369,9 +369,9 @@ bdg_status bdg_plan_create(bdg_plan_t* out, const bdg_params* p, const double* V
       return fail(nullptr, e__ == cudaErrorMemoryAllocation ? BDG_ERR_NOMEM : BDG_ERR_CUDA, m__); \
     }                                                                                        \
   } while (0)
-  CREATE_TRY(cudaMalloc(&plan->phiv64, sizeof(double4) * np));
+  CREATE_TRY(cudaMalloc(&plan->phiv64, sizeof(dquad) * np));
   CREATE_TRY(cudaMalloc(&plan->phiv32, sizeof(float4) * np));
-  CREATE_TRY(cudaMemcpyAsync(plan->phiv64, h64.data(), sizeof(double4) * np, cudaMemcpyHostToDevice, s));
+  CREATE_TRY(cudaMemcpyAsync(plan->phiv64, h64.data(), sizeof(dquad) * np, cudaMemcpyHostToDevice, s));
   CREATE_TRY(cudaMemcpyAsync(plan->phiv32, h32.data(), sizeof(float4) * np, cudaMemcpyHostToDevice, s));
   for (int a = 0; a < g.dim; ++a) {
     std::vector<double> re, im;

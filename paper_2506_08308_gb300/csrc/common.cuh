@@ -15,9 +15,11 @@ namespace bdg {
 // ---------------------------------------------------------------------------
 // complex arithmetic on float2 / double2
 // ---------------------------------------------------------------------------
+// Q: four reals per grid node, (phi_1, phi_0, phi_-1, V).
+struct __align__(32) dquad { double x, y, z, w; };
 template <typename R> struct CT;
 template <> struct CT<float> { typedef float2 T; typedef float4 Q; };
-template <> struct CT<double> { typedef double2 T; typedef double4 Q; };
+template <> struct CT<double> { typedef double2 T; typedef dquad Q; };
 
 __host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
 __host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
@@ -86,7 +88,7 @@ struct bdg_plan_s {
   double mu[3];
   int device;
   // device data
-  double4* phiv64 = nullptr;   // (phi_1, phi_0, phi_-1, V) per node, FP64
+  bdg::dquad* phiv64 = nullptr;   // (phi_1, phi_0, phi_-1, V) per node, FP64
   float4* phiv32 = nullptr;    // the same rounded to FP32
   double2* tw64[3] = {nullptr, nullptr, nullptr};  // W_N^r = exp(-2 pi i r / N), r < N
   float2* tw32[3] = {nullptr, nullptr, nullptr};

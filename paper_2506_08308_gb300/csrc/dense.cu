@@ -1,0 +1,434 @@
+// Small dense FP64 kernels: GEMM, symmetric eigen-decomposition (FP32
+// Jacobi + FP64 Ogita-Aishima refinement), scaling.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "dense.cuh"
+
+namespace bdg {
+
+namespace {
+
+constexpr int TB = 16;
+
+__global__ void k_dgemm(bool ta, bool tb, int m, int n, int k, double alpha, const double* __restrict__ A,
+                        int lda, const double* __restrict__ B, int ldb, double beta, double* __restrict__ C,
+                        int ldc) {
+  __shared__ double sA[TB][TB + 1];
+  __shared__ double sB[TB][TB + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.y * TB + ty, j = blockIdx.x * TB + tx;
+  double acc = 0.0;
+  for (int l0 = 0; l0 < k; l0 += TB) {
+    {  // A tile: rows i (block), cols l0 + tx
+      const int ii = blockIdx.y * TB + ty, ll = l0 + tx;
+      double v = 0.0;
+      if (ii < m && ll < k) v = ta ? A[(long long)ll * lda + ii] : A[(long long)ii * lda + ll];
+      sA[ty][tx] = v;
+    }
+    {  // B tile: rows l0 + ty, cols j
+      const int ll = l0 + ty, jj = blockIdx.x * TB + tx;
+      double v = 0.0;
+      if (ll < k && jj < n) v = tb ? B[(long long)jj * ldb + ll] : B[(long long)ll * ldb + jj];
+      sB[ty][tx] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < TB; ++l) acc = fma(sA[ty][l], sB[l][tx], acc);
+    __syncthreads();
+  }
+  if (i < m && j < n) {
+    double* c = C + (long long)i * ldc + j;
+    *c = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * *c);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Parallel cyclic Jacobi (FP32) on one CTA: round-robin ordering, each round
+// rotates n/2 disjoint (p, q) planes, rows then columns.  Rotation of
+// Golub & Van Loan (sym.schur2): tau = (a_qq - a_pp) / (2 a_pq),
+// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1+t^2), s = t c.
+// Output ascending eigenvalues and the matching columns of V (FP64 copies).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_jacobi(int n, const double* __restrict__ Ag, int lda,
+                                                 double* __restrict__ w, double* __restrict__ Vg,
+                                                 int max_sweeps) {
+  extern __shared__ float sm[];
+  const int ld = n + 1;
+  float* A = sm;                 // [n][ld]
+  float* V = A + n * ld;         // [n][ld]
+  float* cs = V + n * ld;        // [npair][2]
+  int* pq = (int*)(cs + 2 * (n / 2 + 1));  // [npair][2]
+  float* red = (float*)(pq + 2 * (n / 2 + 1));  // [64]
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int np2 = (n + 1) & ~1;  // even count including a dummy index
+  const int npair = np2 / 2;
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, j = e - i * n;
+    A[i * ld + j] = (float)Ag[(long long)i * lda + j];
+    V[i * ld + j] = (i == j) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    // off-diagonal and total Frobenius norms
+    float off = 0.f, tot = 0.f;
+    for (int e = tid; e < n * n; e += nt) {
+      const int i = e / n, j = e - i * n;
+      const float v = A[i * ld + j];
+      tot += v * v;
+      if (i != j) off += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if ((tid & 31) == 0) { red[tid >> 5] = off; red[32 + (tid >> 5)] = tot; }
+    __syncthreads();
+    if (tid == 0) {
+      float so = 0.f, st = 0.f;
+      for (int q = 0; q < (nt + 31) / 32; ++q) { so += red[q]; st += red[32 + q]; }
+      red[0] = so;
+      red[32] = st;
+    }
+    __syncthreads();
+    const bool done = red[0] <= 1e-12f * red[32];
+    __syncthreads();
+    if (done) break;
+    for (int r = 0; r < np2 - 1; ++r) {
+      if (tid < npair) {
+        const int k = tid;
+        int p = (r + k) % (np2 - 1);
+        int q = (k == 0) ? (np2 - 1) : (r - k + np2 - 1) % (np2 - 1);
+        if (p > q) { const int t = p; p = q; q = t; }
+        float c = 1.f, s = 0.f;
+        if (q < n) {
+          const float apq = A[p * ld + q];
+          const float app = A[p * ld + p], aqq = A[q * ld + q];
+          if (fabsf(apq) > 1e-30f && fabsf(apq) > 1e-9f * sqrtf(fabsf(app * aqq))) {
+            const float tau = (aqq - app) / (2.f * apq);
+            const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            c = rsqrtf(1.f + t * t);
+            s = t * c;
+          }
+        } else {
+          q = p;  // dummy: no rotation
+        }
+        pq[2 * k] = p;
+        pq[2 * k + 1] = q;
+        cs[2 * k] = c;
+        cs[2 * k + 1] = s;
+      }
+      __syncthreads();
+      // rows: (row_p, row_q) <- (c row_p - s row_q, s row_p + c row_q)
+      for (int e = tid; e < npair * n; e += nt) {
+        const int k = e / n, j = e - k * n;
+        const int p = pq[2 * k], q = pq[2 * k + 1];
+        if (p == q) continue;
+        const float c = cs[2 * k], s = cs[2 * k + 1];
+        const float ap = A[p * ld + j], aq = A[q * ld + j];
+        A[p * ld + j] = c * ap - s * aq;
+        A[q * ld + j] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns of A and V
+      for (int e = tid; e < npair * n; e += nt) {
+        const int k = e / n, i = e - k * n;
+        const int p = pq[2 * k], q = pq[2 * k + 1];
+        if (p == q) continue;
+        const float c = cs[2 * k], s = cs[2 * k + 1];
+        const float ap = A[i * ld + p], aq = A[i * ld + q];
+        A[i * ld + p] = c * ap - s * aq;
+        A[i * ld + q] = s * ap + c * aq;
+        const float vp = V[i * ld + p], vq = V[i * ld + q];
+        V[i * ld + p] = c * vp - s * vq;
+        V[i * ld + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  // ascending order by rank of the diagonal
+  for (int j = tid; j < n; j += nt) {
+    const float dj = A[j * ld + j];
+    int rank = 0;
+    for (int l = 0; l < n; ++l) {
+      const float dl = A[l * ld + l];
+      rank += (dl < dj) || (dl == dj && l < j);
+    }
+    w[rank] = (double)dj;
+    for (int i = 0; i < n; ++i) Vg[(long long)i * n + rank] = (double)V[i * ld + j];
+  }
+}
+
+// One Ogita-Aishima correction (SIAM J. Sci. Comput. 2018), given R = X^T X
+// and S = X^T A X: lam_i = s_ii / (1 - r_ii), with r = I - X^T X;
+// E_ij = (s_ij + lam_j r_ij) / (lam_j - lam_i) for pairs the current X
+// resolves, else r_ij / 2 (orthogonalization only).  A pair counts as
+// resolved when its corrections are small, |E_ij|, |E_ji| < 1/100, and its gap is above
+// the rounding level of S (16 eps sqrt(n) |A|_F).  The pairwise test replaces the
+// paper's global threshold 2 (|S - diag(lam)| + |A| |R|), which for graded
+// spectra lumps every eigenvalue below eps_32 |A| into one cluster and stalls
+// the refinement there.  On entry R holds X^T X; E is written over S.
+__global__ void __launch_bounds__(1024) k_oa_correction(int n, double* __restrict__ R,
+                                                        double* __restrict__ S,
+                                                        const double* __restrict__ anorm_p,
+                                                        double* __restrict__ lam) {
+  const double anorm = *anorm_p;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // Symmetrize both products first: X^T (A X) carries a rounding asymmetry of
+  // about eps n |A|, and the antisymmetric part of S would enter the
+  // correction as (s_ij - s_ji) / (lam_j - lam_i) -- a loss of orthogonality
+  // of eps n |A| / gap for small, graded eigenvalues.
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, j = e - i * n;
+    if (i > j) continue;
+    const double r = 0.5 * (R[e] + R[j * n + i]);
+    const double sv = 0.5 * (S[e] + S[j * n + i]);
+    R[e] = (i == j ? 1.0 : 0.0) - r;
+    R[j * n + i] = R[e];
+    S[e] = sv;
+    S[j * n + i] = sv;
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) lam[i] = S[i * n + i] / (1.0 - R[i * n + i]);
+  __syncthreads();
+  const double floor_gap = 16.0 * 2.220446049250313e-16 * sqrt((double)n) * anorm;
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, j = e - i * n;
+    const double r = R[e];
+    double ev = 0.5 * r;
+    if (i != j) {
+      // the test is symmetric in (i, j) so that E_ij + E_ji = r_ij holds for
+      // every pair and the update stays orthogonal to first order
+      const double num = S[e] + lam[j] * r;
+      const double numt = S[e] + lam[i] * r;
+      const double den = lam[j] - lam[i];
+      if (fabs(den) > floor_gap && 100.0 * fmax(fabs(num), fabs(numt)) < fabs(den)) ev = num / den;
+    }
+    S[e] = ev;
+  }
+}
+
+__global__ void k_frob(int n, const double* __restrict__ A, int lda, double* __restrict__ out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e - i * n;
+    const double v = A[(long long)i * lda + j];
+    s += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x + 31) / 32; ++q) t += red[q];
+    *out = sqrt(t);
+  }
+}
+
+// sort (w, V columns) ascending after refinement (n small; one CTA)
+__global__ void k_sort_eig(int n, const double* __restrict__ w, const double* __restrict__ V,
+                           double* __restrict__ w2, double* __restrict__ V2) {
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double dj = w[j];
+    int rank = 0;
+    for (int l = 0; l < n; ++l) rank += (w[l] < dj) || (w[l] == dj && l < j);
+    w2[rank] = dj;
+    for (int i = 0; i < n; ++i) V2[(long long)i * n + rank] = V[(long long)i * n + j];
+  }
+}
+
+__global__ void k_dscale(int m, int n, const double* __restrict__ A, int lda, const double* __restrict__ dl,
+                         const double* __restrict__ dr, double* __restrict__ B, int ldb) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * n; e += gridDim.x * blockDim.x) {
+    const int i = e / n, j = e - i * n;
+    double v = A[(long long)i * lda + j];
+    if (dl) v *= dl[i];
+    if (dr) v *= dr[j];
+    B[(long long)i * ldb + j] = v;
+  }
+}
+
+__global__ void k_dsym(int n, double* A, int lda) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+    const int i = e / n, j = e - i * n;
+    if (j >= i) continue;
+    const double v = 0.5 * (A[(long long)i * lda + j] + A[(long long)j * lda + i]);
+    A[(long long)i * lda + j] = v;
+    A[(long long)j * lda + i] = v;
+  }
+}
+
+__global__ void k_dzero(int m, int n, double* B, int ldb) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * n; e += gridDim.x * blockDim.x) {
+    const int i = e / n, j = e - i * n;
+    B[(long long)i * ldb + j] = 0.0;
+  }
+}
+
+}  // namespace
+
+cudaError_t dsym_small(int n, double* A, int lda, cudaStream_t s) {
+  if (n <= 1) return cudaSuccess;
+  k_dsym<<<(n * n + 255) / 256, 256, 0, s>>>(n, A, lda);
+  return cudaGetLastError();
+}
+
+cudaError_t dzero_small(int m, int n, double* B, int ldb, cudaStream_t s) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  k_dzero<<<(m * n + 255) / 256, 256, 0, s>>>(m, n, B, ldb);
+  return cudaGetLastError();
+}
+
+cudaError_t dgemm_small(bool ta, bool tb, int m, int n, int k, double alpha, const double* A, int lda,
+                        const double* B, int ldb, double beta, double* C, int ldc, cudaStream_t s) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  dim3 grid((n + TB - 1) / TB, (m + TB - 1) / TB), block(TB, TB);
+  k_dgemm<<<grid, block, 0, s>>>(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+  return cudaGetLastError();
+}
+
+cudaError_t dscale_small(int m, int n, const double* A, int lda, const double* dl, const double* dr,
+                         double* B, int ldb, cudaStream_t s) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  k_dscale<<<(m * n + 255) / 256, 256, 0, s>>>(m, n, A, lda, dl, dr, B, ldb);
+  return cudaGetLastError();
+}
+
+
+__global__ void k_add_diag(int n, double* A, int lda, double c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) A[(long long)i * lda + i] += c;
+}
+// M = (3 I - G) / 2, one Newton-Schulz step toward (G)^-1/2 for G = V^T V near I
+__global__ void k_newton_schulz(int n, double* G) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+    const int i = e / n, j = e - i * n;
+    G[e] = (i == j ? 1.5 : 0.0) - 0.5 * G[e];
+  }
+}
+__global__ void k_add_vec(int n, double* w, double c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) w[i] += c;
+}
+
+size_t eigh_workspace_doubles(int n) { return (size_t)48 * n * n + 128 * n + 256; }
+
+namespace {
+
+// FP32 Jacobi start for A (n x n, lda) into (w, V), with clusters resolved
+// by recursion.  FP32 separates eigenvalues only down to about 1e-7 max|w|;
+// every run of consecutive eigenvalues closer than 1e-4 max|w| (a cluster
+// around its midpoint c -- which includes the eigenvalues near zero of a
+// graded matrix) is re-solved on the FP64 projection V_s^T (A - c I) V_s,
+// whose norm is about the spread, and rotated back.  Runs are disjoint, so
+// the workspace is reused from one to the next.
+cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double* V, double* ws, int depth,
+                              cudaStream_t s) {
+  const size_t sm = sizeof(float) * (2 * (size_t)n * (n + 1) + 2 * (n / 2 + 1)) +
+                    sizeof(int) * 2 * (n / 2 + 1) + sizeof(float) * 64;
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_jacobi<<<1, 1024, sm, s>>>(n, A, lda, w, V, 30);
+  if ((e = cudaGetLastError())) return e;
+  if (depth >= 4 || n < 2) return cudaSuccess;
+  std::vector<double> hw(n);
+  if ((e = cudaMemcpyAsync(hw.data(), w, sizeof(double) * n, cudaMemcpyDeviceToHost, s))) return e;
+  if ((e = cudaStreamSynchronize(s))) return e;
+  double amax = 0.0;
+  for (double v : hw) amax = std::max(amax, std::fabs(v));
+  if (!(amax > 0)) return cudaSuccess;
+  const double tau = 1e-4 * amax;
+  for (int i0 = 0; i0 < n;) {
+    int i1 = i0 + 1;
+    while (i1 < n && hw[i1] - hw[i1 - 1] < tau) ++i1;
+    const int ns = i1 - i0;
+    if (ns >= 2 && hw[i1 - 1] > hw[i0]) {
+      const double c = 0.5 * (hw[i0] + hw[i1 - 1]);  // midpoint: the shifted norm is half the spread
+      double* Vs = ws;                         // n x ns
+      double* AVs = Vs + (size_t)n * ns;       // n x ns
+      double* As = AVs + (size_t)n * ns;       // ns x ns
+      double* w2 = As + (size_t)ns * ns;       // ns
+      double* V2 = w2 + ns + 8;                // ns x ns
+      double* Vn = V2 + (size_t)ns * ns;       // n x ns
+      double* rest = Vn + (size_t)n * ns;
+      // V's columns i0 .. i1-1 are contiguous: gather with a strided copy
+      if ((e = cudaMemcpy2DAsync(Vs, sizeof(double) * ns, V + i0, sizeof(double) * n, sizeof(double) * ns, n,
+                                 cudaMemcpyDeviceToDevice, s)))
+        return e;
+      // FP64 orthonormalization of the FP32 columns (two Newton-Schulz
+      // steps): with c != 0 the projection would otherwise carry
+      // c (V^T V - I) ~ 1e-7 c, which can exceed the spread being resolved
+      for (int it = 0; it < 2; ++it) {
+        if ((e = dgemm_small(true, false, ns, ns, n, 1.0, Vs, ns, Vs, ns, 0.0, As, ns, s))) return e;
+        k_newton_schulz<<<(ns * ns + 255) / 256, 256, 0, s>>>(ns, As);
+        if ((e = cudaGetLastError())) return e;
+        if ((e = dgemm_small(false, false, n, ns, ns, 1.0, Vs, ns, As, ns, 0.0, Vn, ns, s))) return e;
+        if ((e = cudaMemcpyAsync(Vs, Vn, sizeof(double) * n * ns, cudaMemcpyDeviceToDevice, s))) return e;
+      }
+      if ((e = dgemm_small(false, false, n, ns, n, 1.0, A, lda, Vs, ns, 0.0, AVs, ns, s))) return e;
+      if ((e = dgemm_small(true, false, ns, ns, n, 1.0, Vs, ns, AVs, ns, 0.0, As, ns, s))) return e;
+      if ((e = dsym_small(ns, As, ns, s))) return e;
+      k_add_diag<<<(ns + 127) / 128, 128, 0, s>>>(ns, As, ns, -c);
+      if ((e = cudaGetLastError())) return e;
+      if ((e = jacobi_multilevel(ns, As, ns, w2, V2, rest, depth + 1, s))) return e;
+      k_add_vec<<<(ns + 127) / 128, 128, 0, s>>>(ns, w2, c);
+      if ((e = cudaGetLastError())) return e;
+      if ((e = dgemm_small(false, false, n, ns, ns, 1.0, Vs, ns, V2, ns, 0.0, Vn, ns, s))) return e;
+      if ((e = cudaMemcpy2DAsync(V + i0, sizeof(double) * n, Vn, sizeof(double) * ns, sizeof(double) * ns, n,
+                                 cudaMemcpyDeviceToDevice, s)))
+        return e;
+      if ((e = cudaMemcpyAsync(w + i0, w2, sizeof(double) * ns, cudaMemcpyDeviceToDevice, s))) return e;
+    }
+    i0 = i1;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t eigh(int n, const double* A, int lda, double* w, double* V, double* ws, int refine_steps,
+                 cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (n > SMALL_MAX) return cudaErrorInvalidValue;
+  cudaError_t e;
+  double* X = ws;                 // n x n current eigenvectors
+  double* X2 = X + n * n;         // n x n
+  double* R = X2 + n * n;         // n x n
+  double* S = R + n * n;          // n x n
+  double* AX = S + n * n;         // n x n
+  double* lam = AX + n * n;       // n
+  double* lam2 = lam + n;         // n
+  double* anorm = lam2 + n;       // 8
+  double* rest = anorm + 8;
+  if ((e = jacobi_multilevel(n, A, lda, lam2, X, rest, 0, s))) return e;
+  k_frob<<<1, 1024, 0, s>>>(n, A, lda, anorm);
+  double* cur = X;
+  double* nxt = X2;
+  for (int it = 0; it < refine_steps; ++it) {
+    if ((e = dgemm_small(true, false, n, n, n, 1.0, cur, n, cur, n, 0.0, R, n, s))) return e;
+    if ((e = dgemm_small(false, false, n, n, n, 1.0, A, lda, cur, n, 0.0, AX, n, s))) return e;
+    if ((e = dgemm_small(true, false, n, n, n, 1.0, cur, n, AX, n, 0.0, S, n, s))) return e;
+    k_oa_correction<<<1, 1024, 0, s>>>(n, R, S, anorm, lam);
+    if ((e = cudaGetLastError())) return e;
+    // X <- X + X E
+    if ((e = cudaMemcpyAsync(nxt, cur, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s))) return e;
+    if ((e = dgemm_small(false, false, n, n, n, 1.0, cur, n, S, n, 1.0, nxt, n, s))) return e;
+    double* t = cur; cur = nxt; nxt = t;
+  }
+  // Rotations driven by rounding noise (pairs just above the gap floor)
+  // leave a second-order loss of orthogonality; two Newton-Schulz steps
+  // X <- X (3 I - X^T X) / 2 remove it without rotating.
+  for (int it = 0; refine_steps > 0 && it < 2; ++it) {
+    if ((e = dgemm_small(true, false, n, n, n, 1.0, cur, n, cur, n, 0.0, R, n, s))) return e;
+    k_newton_schulz<<<(n * n + 255) / 256, 256, 0, s>>>(n, R);
+    if ((e = cudaGetLastError())) return e;
+    if ((e = dgemm_small(false, false, n, n, n, 1.0, cur, n, R, n, 0.0, nxt, n, s))) return e;
+    double* t = cur; cur = nxt; nxt = t;
+  }
+  k_sort_eig<<<1, 256, 0, s>>>(n, refine_steps > 0 ? lam : lam2, cur, w, V);
+  return cudaGetLastError();
+}
+
+}  // namespace bdg

@@ -1,0 +1,106 @@
+"""Parity of bdg_solve (CUDA) with the oracle's dense FP64 solution of
+eq. lrep-d: the k smallest positive excitations to 1e-10 relative, the
+amplitudes per degenerate cluster to 1e-8 (projector metric of Section 4.1),
+residuals <= 1e-10 in FP64, and the normalization / bi-orthogonality
+h^d (u_i.u_j - v_i.v_j) = delta_ij (eq. constrain, Theorem
+"Biorthogonality"); FP64 and mixed precision, 1-D and 2-D, odd and even
+block sizes, a start block passed in and the internal seeded one."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import make_plan, need_torch_cuda, oracle_problem
+
+pytestmark = pytest.mark.gpu
+
+W1 = synth.Workload("s1d_n64", (64,), (-8.0,), (8.0,), (1.0,), 10.0, -1.0, 0.0, 0.0, k=8, m=12,
+                    gs_seed=101, block_seed=7)
+W1Q = synth.Workload("s1d_n64_q", (64,), (-8.0,), (8.0,), (1.0,), 10.0, -1.0, 0.0, 0.1, k=8, m=11,
+                     gs_seed=102, block_seed=9)
+W2 = synth.Workload("s2d_16", (16, 16), (-6.0, -6.0), (6.0, 6.0), (1.0, 1.4), 12.0, -1.0, 0.05, 0.3, k=10, m=14,
+                    gs_seed=8, block_seed=3)
+WC1 = synth.CONFIG1
+
+
+def _dense(op, k):
+    from oracle import lrep
+    return lrep.dense_solve_fg(op, k + 6)
+
+
+def _check(w, op, om, UV, resid, k, dense):
+    from oracle import lrep
+    om_d, F, G = dense
+    assert np.all(resid[:k] <= 1e-10), resid
+    assert np.allclose(om[:k], om_d[:k], rtol=1e-10, atol=0), (om[:k], om_d[:k])
+    U = UV[:k, :3].reshape(k, -1)
+    V = UV[:k, 3:].reshape(k, -1)
+    hd = lrep.weight(w)
+    gram = hd * (U @ U.T - V @ V.T)
+    assert np.allclose(gram, np.eye(k), atol=1e-8), np.abs(gram - np.eye(k)).max()
+    # amplitudes per cluster of (relative gap < 1e-8) eigenvalues, the cluster
+    # fully inside the first k
+    Ud = (F + G)[:, :, :].reshape(len(om_d), -1)
+    Vd = (F - G).reshape(len(om_d), -1)
+    i = 0
+    while i < k:
+        j = i + 1
+        while j < len(om_d) and abs(om_d[j] - om_d[i]) < 1e-8 * om_d[i]:
+            j += 1
+        if j <= k:
+            Q, _ = np.linalg.qr(np.concatenate([Ud[i:j], Vd[i:j]], axis=1).T)
+            X = np.concatenate([U[i:j], V[i:j]], axis=1).T
+            err = np.linalg.norm(X - Q @ (Q.T @ X)) / np.linalg.norm(X)
+            assert err < 1e-8, (i, j, err)
+        i = j
+    r = lrep.residual_uv(op, UV[:k], om[:k])
+    assert r.max() < 1e-9, r
+
+
+@pytest.mark.parametrize("w", [W1, W1Q, W2], ids=lambda w: w.name)
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_matches_dense(w, prec):
+    torch = need_torch_cuda()
+    from paper_2506_08308_gb300 import bdg
+    V, phi, mu, op = oracle_problem(w)
+    plan = make_plan(w, V, phi, prec=bdg.FP64 if prec == "fp64" else bdg.MIXED, tol=1e-10, maxit=600)
+    X0 = torch.from_numpy(synth.random_block(w, w.m, complex_=True)).cuda()
+    om, UV, resid, nconv = plan.solve(w.k, w.m, X0=X0)
+    assert nconv == w.k
+    _check(w, op, om, UV.cpu().numpy().real, resid, w.k, _dense(op, w.k))
+    st = plan.stats()
+    assert st["iterations"] > 0
+    if prec == "mixed":
+        assert st["iterations_fp32"] > 0 and st["applies_fp32"] > 0
+    plan.close()
+
+
+def test_solve_config1_full_size():
+    """The 1-D workload as specified: N = 256, k = 16, m = 24, FP64, seeded
+    internal start block."""
+    torch = need_torch_cuda()
+    from paper_2506_08308_gb300 import bdg
+    w = WC1
+    V, phi, mu, op = oracle_problem(w)
+    plan = make_plan(w, V, phi, prec=bdg.FP64, tol=1e-10, maxit=800, seed=w.block_seed)
+    om, UV, resid, nconv = plan.solve(w.k, w.m)
+    assert nconv == w.k
+    dense = _dense(op, w.k)
+    _check(w, op, om, UV.cpu().numpy().real, resid, w.k, dense)
+    # the Kohn mode omega = gamma_x = 1 is among the excitations (Theorem
+    # "Analytical eigenpairs")
+    assert np.min(np.abs(om - 1.0)) < 1e-9
+    plan.close()
+
+
+def test_solve_rejects_bad_sizes():
+    need_torch_cuda()
+    from paper_2506_08308_gb300 import bdg
+    V, phi, mu, op = oracle_problem(W1)
+    plan = make_plan(W1, V, phi)
+    with pytest.raises(bdg.BdgError) as e:
+        plan.solve(5, 4)
+    assert e.value.status == bdg.ERR_INVALID
+    with pytest.raises(bdg.BdgError) as e:
+        plan.solve(8, 200)
+    assert e.value.status == bdg.ERR_UNSUPPORTED
+    plan.close()
