@@ -542,8 +542,7 @@ class Solver {
     double* Z = dmat_[MAT_E];
     std::vector<double> w2;
     if ((st = eigh_dev(r, C, r, dvec_, Z, w2))) return st;
-    const double cnorm = std::max(std::fabs(w2[0]), std::fabs(w2[r - 1]));
-    const double cut = std::max(zero_tol2_, 1e-13 * cnorm);
+    const double cut = zero_tol2_;
     int j0 = 0;
     while (j0 < r && !(w2[j0] > cut)) ++j0;
     const int mm = std::min(mmax, r - j0);
