@@ -1081,9 +1081,5 @@ bdg_status bdg_biortho(bdg_plan_t plan, int, void*, void*, int, const void*, con
   return fail(plan, BDG_ERR_UNSUPPORTED, "bdg_biortho not built yet");
 }
 
-bdg_status bdg_ground_state(const bdg_params*, double, const double*, const double*, double, int, double*,
-                            double*, double*, int*, void*) {
-  return fail(nullptr, BDG_ERR_UNSUPPORTED, "bdg_ground_state not built yet");
-}
 
 }  // extern "C"
