@@ -1,0 +1,397 @@
+"""Benchmark of the spin-1 BdG hot path on one or more GPUs.
+
+One step is one bdg_solve of the 2-D workload (256^2 Fourier grid, box
+[-12,12)^2, isotropic trap, beta_n = 100, beta_s = -2, q = 0.1): the 32
+smallest positive excitations at relative residual 1e-10, block 48, mixed
+precision (FP32 bulk, FP64 refinement).  The ground state comes from
+bdg_ground_state on the device before timing; the start block is seeded.
+
+Printed (rank 0, one JSON line): converged eigenpairs/s over all ranks
+(value), the same through host buffers (e2e), the FP64-only solver on the
+same problem, the BdG-apply roofline of the dominant kernel, the CPU oracle
+baseline, SM clocks sampled during the timed region, and kernel launches.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank solves its own independent instance (weak scaling,
+no collective on the data path).
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "BdG-apply HBM GB/s; converged eigenpairs/s at resid 1e-10, mixed vs FP64"
+UNIT = "eigenpairs/s"
+W = synth.CONFIG2
+TOL = 1e-10
+# Iterations the block solver needs on this workload (the device mixed solve
+# from the seeded start block); the CPU timings are extrapolated to it.
+SOLVE_ITERATIONS = 165
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--fp64-maxit", type=int, default=300,
+                    help="iteration cap of the FP64-only comparison solve (0: skip)")
+    ap.add_argument("--cpu-iters", type=int, default=2,
+                    help="oracle solver iterations in the CPU baseline sample (0: skip)")
+    ap.add_argument("--skip-e2e", action="store_true", help="leave out the host-buffer pass")
+    ap.add_argument("--skip-launch-count", action="store_true", help="leave out the profiler pass")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        rows = [r for r in self.rows if r[0] == str(self.gpu)] or self.rows
+        mhz = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(self.NAMES, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(mhz)) if mhz else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def source_digest(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+APPLY_SOURCES = ["paper_2506_08308_gb300/csrc/apply_impl.cuh", "paper_2506_08308_gb300/csrc/fft.cuh",
+                 "paper_2506_08308_gb300/csrc/apply_f32.cu", "paper_2506_08308_gb300/csrc/common.cuh"]
+
+
+def apply_traffic():
+    """DRAM bytes per call of the FP32 block product from the committed ncu
+    summary, or None when the kernels changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = t.get("bdg_apply_c64_2d_n256")
+    if not e or e.get("src_digest") != source_digest(APPLY_SOURCES):
+        return None
+    return e.get("dram_bytes_per_call")
+
+
+# ------------------------------------------------------------ CPU oracle
+def cpu_oracle_sample(iters, n_iter_solve):
+    """The oracle's FP64 block solver timed for `iters` iterations on the full
+    workload on the host cores; eigenpairs/s extrapolated to n_iter_solve
+    iterations.  The operator is built from the seeded start spinor (the
+    spinor's values do not change the cost of an iteration)."""
+    from oracle import apply as ap
+    from oracle import lrep
+    V = synth.potential(W)
+    phi = synth.initial_spinor(W)
+    phi = phi / np.sqrt(np.prod(W.h) * np.sum(phi ** 2))
+    mu = np.array([1.0, 1.0, 1.0])
+    op = ap.Operator(W, phi, V, mu)
+    Zf = phi.reshape(-1, 1) / np.linalg.norm(phi)
+    Zg = np.zeros((Zf.shape[0], 0))
+    X0 = synth.random_block(W, W.m, complex_=False)
+    t0 = time.perf_counter()
+    lrep.solve_iterative(op, W.k, W.m, X0, Zf, Zg, tol=TOL, maxit=iters)
+    dt = time.perf_counter() - t0
+    per_it = dt / iters
+    value = W.k / (per_it * n_iter_solve)
+    return {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"{iters} iterations of the oracle's FP64 block solver on the full {W.name} "
+                       f"workload (k={W.k}, m={W.m}) in {dt:.1f} s; eigenpairs/s extrapolated to "
+                       f"{n_iter_solve} iterations; numpy/scipy with default threads"),
+            "seconds_per_iteration": per_it}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_oracle_sample(1, SOLVE_ITERATIONS)
+    iters = max(args.cpu_iters, 1)
+    vals, secs, s = [], [], None
+    for _ in range(args.steps):
+        s = cpu_oracle_sample(iters, SOLVE_ITERATIONS)
+        vals.append(s["value"])
+        secs.append(s["seconds_per_iteration"] * SOLVE_ITERATIONS)
+    value = float(np.median(vals))
+    cb = {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": s["sample"]}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.median(secs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)",
+            "config": dict(synth.describe(W), workload=W.name, precision="fp64 (oracle)"),
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ GPU arm
+def end_to_end(args, plan, X0h, X0, w, stream, barrier, max_over_ranks, world):
+    """The same solves through host buffers: every step copies the start block
+    from pinned host memory and the eigenvectors back to pinned host memory
+    inside the timed region."""
+    import torch
+    X0pin = torch.from_numpy(X0h).pin_memory()
+    UVpin = torch.empty((w.k, 6, w.npts), dtype=torch.complex128).pin_memory()
+    Xdev = torch.empty_like(X0)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    conv = 0
+    for _ in range(args.steps):
+        Xdev.copy_(X0pin, non_blocking=True)
+        om, UV, resid, nconv = plan.solve(w.k, w.m, X0=Xdev, want_vectors=True)
+        UVpin.copy_(UV, non_blocking=True)
+        conv += nconv
+    e1.record(stream)
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    return {"value": conv * world / (ms / 1000.0), "unit": UNIT,
+            "h2d_bytes_per_step": int(X0pin.numel() * X0pin.element_size()),
+            "d2h_bytes_per_step": int(UVpin.numel() * UVpin.element_size()) + 2 * 8 * w.k}
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2506_08308_gb300 import bdg
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- inputs (untimed): ground state on the device, seeded start block
+    w = W
+    V = synth.potential(w)
+    phi, mu, gres, git = bdg.ground_state(bdg.params_from(w), w.M, V, synth.initial_spinor(w), tol=1e-12)
+    seed = w.block_seed + 7919 * rank          # an independent instance per rank
+    X0h = synth.random_block(w, w.m, complex_=True, seed=seed)
+    X0 = torch.from_numpy(X0h).to(dev)
+    plan = bdg.Plan(bdg.params_from(w, prec=bdg.MIXED, tol=TOL, maxit=3000), V, phi.reshape(-1))
+
+    def step():
+        om, UV, resid, nconv = plan.solve(w.k, w.m, X0=X0, want_vectors=True)
+        return nconv
+
+    for _ in range(args.warmup):
+        step()
+    # ---- timed region: K solves, inputs resident in HBM
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    sampler = ClockSampler(int(cvd) if cvd.isdigit() else local)
+    barrier()
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    conv = 0
+    for _ in range(args.steps):
+        conv += step()
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = max_over_ranks(ev0.elapsed_time(ev1))
+    value = conv * world / (ms / 1000.0)
+    stats = plan.stats()
+
+    e2e = None
+    if not args.skip_e2e:
+        e2e = end_to_end(args, plan, X0h, X0, w, stream, barrier, max_over_ranks, world)
+
+    # ---- FP64-only comparison on the same instance (one capped solve)
+    fp64 = None
+    if args.fp64_maxit > 0:
+        plan64 = bdg.Plan(bdg.params_from(w, prec=bdg.FP64, tol=TOL, maxit=args.fp64_maxit), V,
+                          phi.reshape(-1))
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        om, UV, resid, nconv64 = plan64.solve(w.k, w.m, X0=X0, want_vectors=True, allow_not_converged=True)
+        f1.record(stream)
+        barrier()
+        ms64 = max_over_ranks(f0.elapsed_time(f1))
+        st64 = plan64.stats()
+        fp64 = {"value": nconv64 * world / (ms64 / 1000.0), "unit": UNIT, "converged": int(nconv64),
+                "of": w.k, "iterations": st64["iterations"], "maxit": args.fp64_maxit,
+                "seconds": ms64 / 1000.0, "worst_resid": float(np.max(resid))}
+        plan64.close()
+
+    # ---- roofline of the dominant kernel: the FP32 block product
+    # (line FFTs + k-space multiply + 6x6 coupling), timed alone
+    peaks, peak_kind = measured_peaks()
+    xa = torch.from_numpy(synth.random_block(w, w.m, complex_=True, seed=5)).to(dev).to(torch.complex64)
+    ya = torch.empty_like(xa)
+    for _ in range(3):
+        plan.apply(xa, bdg.FG, out=ya)
+    nrep = 20
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a0.record(stream)
+    for _ in range(nrep):
+        plan.apply(xa, bdg.FG, out=ya)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    t_apply = a0.elapsed_time(a1) / nrep / 1000.0
+    alg_bytes = (96 * w.m + 16) * w.npts          # x in + y out (c64, 6 fields) + (Phi, V) FP32 table
+    achieved = alg_bytes / t_apply / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": apply_traffic(),
+                "kernel": "bdg_apply FG c64, m=48 block, 256^2 (row pass + column pass)",
+                "us_per_call": t_apply * 1e6, "algorithmic_bytes_per_call": alg_bytes,
+                "peak_kind": peak_kind + " burst copy"}
+    # the FP64 product, for reference (FP64 ALU-bound on this part)
+    xd = xa.to(torch.complex128)
+    yd = torch.empty_like(xd)
+    plan.apply(xd, bdg.FG, out=yd)
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    for _ in range(5):
+        plan.apply(xd, bdg.FG, out=yd)
+    b1.record(stream)
+    torch.cuda.synchronize()
+    t_apply64 = b0.elapsed_time(b1) / 5 / 1000.0
+
+    # ---- kernel launches of one solve (profiler over one extra, untimed step)
+    launches = None
+    if not args.skip_launch_count:
+        try:
+            from torch.profiler import ProfilerActivity, profile
+            with profile(activities=[ProfilerActivity.CUDA]) as prof:
+                step()
+                torch.cuda.synchronize()
+            per_step = sum(1 for e in prof.events()
+                           if str(getattr(e, "device_type", "")).endswith("CUDA") and "bdg" in e.name)
+            launches = per_step * args.steps if per_step > 0 else None
+        except Exception:  # noqa: BLE001 -- auxiliary evidence only
+            launches = None
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_iters > 0:
+        cpu = cpu_oracle_sample(args.cpu_iters, stats["iterations"])
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic (seeded start block; ground state from bdg_ground_state)",
+                "config": dict(synth.describe(w), workload=w.name, precision="mixed FP32/FP64", tol=TOL,
+                               l2="working set larger than L2 (151 MB c64 block, ~1 GB of bases); no flush",
+                               parallelism=f"{world} independent instance(s)"),
+                "roofline": roofline,
+                "cpu_baseline": cpu,
+                "e2e": e2e,
+                "fp64_solver": fp64,
+                "apply_fp64_us_per_call": t_apply64 * 1e6,
+                "solve_stats": stats,
+                "ground_state": {"residual": gres, "iterations": git},
+                "clocks": clocks,
+                "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
