@@ -173,6 +173,30 @@ bdg_status bdg_ground_state(const bdg_params* p, double M, const double* V, cons
                             double tol, int maxit, double* phi, double* mu, double* resid,
                             int* iters, void* stream);
 
+/*
+ * bdg_chemical_potentials_noalloc -- the chemical potentials mu_j of the
+ * plan's Phi by eq. chem-formula (the values bdg_plan_create computes when
+ * p->mu[j] is NaN), whatever mu the plan itself uses.  The paper has no
+ * counterpart: this entry point exists for callers that must not allocate
+ * device memory during the call (a memory budget or caching allocator that
+ * forbids implicit cudaMalloc, a loop that cannot afford an allocation's
+ * synchronization).  It allocates nothing: its scratch is one fixed device
+ * array of about 3.1 MB inside the library, held by every GPU that loads the
+ * library until the process exits.
+ *   mu     [out, host] double[3].
+ * Limits and caveats:
+ *   - grids of at most 16384 points (e.g. 128^2, 16 x 32^2, or 1-D up to
+ *     1024); larger plans return BDG_ERR_UNSUPPORTED with the limit in
+ *     bdg_last_error.
+ *   - all calls share the array: calls that overlap on the GPU (several
+ *     streams, threads or plans at once) race and must be serialized.
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and should come before any stream capture on
+ *     that device.
+ * The call synchronizes the stream before it returns.
+ */
+bdg_status bdg_chemical_potentials_noalloc(bdg_plan_t plan, double* mu, void* stream);
+
 /* bdg_last_error -- message of the last failing call on plan (NULL: of the
  * last failing plan-less call on this thread).  Never NULL. */
 const char* bdg_last_error(bdg_plan_t plan);

@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "BDG_OK", 1: "BDG_ERR_INVALID", 2: "BDG_ERR_NOMEM", 3: "BDG_E
 
 # every symbol include/bdg.h declares
 EXPORTS = ("bdg_plan_create", "bdg_plan_destroy", "bdg_plan_mu", "bdg_apply", "bdg_biortho",
-           "bdg_solve", "bdg_get_solve_stats", "bdg_ground_state", "bdg_last_error")
+           "bdg_solve", "bdg_get_solve_stats", "bdg_ground_state", "bdg_chemical_potentials_noalloc",
+           "bdg_last_error")
 
 
 class Params(ctypes.Structure):
@@ -74,6 +75,7 @@ def load() -> ctypes.CDLL:
     lib.bdg_get_solve_stats.argtypes = [vp, ctypes.POINTER(SolveStats)]
     lib.bdg_ground_state.argtypes = [ctypes.POINTER(Params), ctypes.c_double, dp, dp, ctypes.c_double,
                                      ctypes.c_int, dp, dp, dp, ip, vp]
+    lib.bdg_chemical_potentials_noalloc.argtypes = [vp, dp, vp]
     lib.bdg_last_error.argtypes = [vp]
     lib.bdg_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -165,6 +167,15 @@ class Plan:
     def mu(self) -> np.ndarray:
         out = np.zeros(3)
         _check(self.lib, self.lib.bdg_plan_mu(self.handle, _dptr(out)), self.handle)
+        return out
+
+    def chemical_potentials_noalloc(self, stream=None) -> np.ndarray:
+        """bdg_chemical_potentials_noalloc: eq. chem-formula mu of the plan's Phi,
+        computed without any device allocation (fixed library-owned scratch;
+        grids of at most 16384 points; overlapping calls race)."""
+        out = np.zeros(3)
+        st = self.lib.bdg_chemical_potentials_noalloc(self.handle, _dptr(out), _stream_handle(stream))
+        _check(self.lib, st, self.handle)
         return out
 
     def apply(self, x, mode: int = UV, out=None, stream=None):
