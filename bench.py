@@ -52,6 +52,8 @@ def parse():
                     help="oracle solver iterations in the CPU baseline sample (0: skip)")
     ap.add_argument("--skip-e2e", action="store_true", help="leave out the host-buffer pass")
     ap.add_argument("--skip-launch-count", action="store_true", help="leave out the profiler pass")
+    ap.add_argument("--apply-only", action="store_true",
+                    help="time only the block product of the workload (profiling aid; no JSON line)")
     return ap.parse_args()
 
 
@@ -228,6 +230,35 @@ def end_to_end(args, plan, X0h, X0, w, stream, barrier, max_over_ranks, world):
             "d2h_bytes_per_step": int(UVpin.numel() * UVpin.element_size()) + 2 * 8 * w.k}
 
 
+def run_apply_only(args):
+    """The FP32 and FP64 block products of the workload alone, on an operator
+    built from the normalised seeded start spinor (the values of Phi do not
+    change the cost); prints one line per precision."""
+    import torch
+    from paper_2506_08308_gb300 import bdg
+    w = W
+    phi = synth.initial_spinor(w)
+    phi = phi / np.sqrt(np.prod(w.h) * np.sum(phi ** 2))
+    plan = bdg.Plan(bdg.params_from(w, mu=(1.0, 1.0, 1.0)), synth.potential(w), phi.reshape(-1))
+    x = torch.from_numpy(synth.random_block(w, w.m, complex_=True, seed=5)).cuda()
+    for dt, bytes_pt in ((torch.complex64, 96), (torch.complex128, 192)):
+        xa = x.to(dt)
+        ya = torch.empty_like(xa)
+        for _ in range(max(args.warmup, 1)):
+            plan.apply(xa, bdg.FG, out=ya)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            plan.apply(xa, bdg.FG, out=ya)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / max(args.steps, 1) / 1000.0
+        print(f"apply {dt} m={w.m} {w.name}: {t * 1e6:.1f} us/call, "
+              f"{(bytes_pt * w.m + bytes_pt // 6) * w.npts / t / 1e9:.0f} GB/s algorithmic", flush=True)
+    plan.close()
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -389,6 +420,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.apply_only:
+        run_apply_only(args)
     else:
         run_ours(args)
 
