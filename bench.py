@@ -375,19 +375,35 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_apply64 = b0.elapsed_time(b1) / 5 / 1000.0
 
-    # ---- kernel launches of one solve (profiler over one extra, untimed step)
-    launches = None
+    # ---- kernel launches and per-kernel device time of one solve, from a
+    # CUPTI trace (torch profiler) over one extra, untimed step
+    launches, shares = None, None
     if not args.skip_launch_count:
         try:
             from torch.profiler import ProfilerActivity, profile
             with profile(activities=[ProfilerActivity.CUDA]) as prof:
                 step()
                 torch.cuda.synchronize()
-            per_step = sum(1 for e in prof.events()
-                           if str(getattr(e, "device_type", "")).endswith("CUDA") and "bdg" in e.name)
-            launches = per_step * args.steps if per_step > 0 else None
+            per_kernel = {}
+            for e in prof.events():
+                if not str(getattr(e, "device_type", "")).endswith("CUDA") or "bdg" not in e.name:
+                    continue
+                t = getattr(e, "device_time", None)
+                if t is None:
+                    t = getattr(e, "cuda_time", 0.0)
+                name = e.name.split("(")[0].replace("void ", "")
+                c, tt = per_kernel.get(name, (0, 0.0))
+                per_kernel[name] = (c + 1, tt + float(t))
+            n = sum(c for c, _ in per_kernel.values())
+            total = sum(t for _, t in per_kernel.values())
+            launches = n * args.steps if n > 0 else None
+            if total > 0:
+                top = sorted(per_kernel.items(), key=lambda kv: -kv[1][1])[:12]
+                shares = {"step_device_ms": total / 1000.0, "launches_per_step": n,
+                          "kernels": [{"name": k, "launches": c, "ms": t / 1000.0, "share": t / total}
+                                      for k, (c, t) in top]}
         except Exception:  # noqa: BLE001 -- auxiliary evidence only
-            launches = None
+            launches, shares = None, None
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_iters > 0:
@@ -409,7 +425,8 @@ def run_ours(args):
                 "solve_stats": stats,
                 "ground_state": {"residual": gres, "iterations": git},
                 "clocks": clocks,
-                "gpu_launches": launches}
+                "gpu_launches": launches,
+                "kernel_shares": shares}
         print(json.dumps(line), flush=True)
     plan.close()
     if dist is not None:
