@@ -19,6 +19,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -391,7 +392,8 @@ def run_ours(args):
                 t = getattr(e, "device_time", None)
                 if t is None:
                     t = getattr(e, "cuda_time", 0.0)
-                name = e.name.split("(")[0].replace("void ", "")
+                mk = re.search(r"(k_\w+(<[^()]*?>)?)\(", e.name)
+                name = mk.group(1) if mk else e.name[:60]
                 c, tt = per_kernel.get(name, (0, 0.0))
                 per_kernel[name] = (c + 1, tt + float(t))
             n = sum(c for c, _ in per_kernel.values())
