@@ -68,6 +68,96 @@ __global__ void __launch_bounds__(256) k_gram_partial(PairBlock<R> A, PairBlock<
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP64 blocks on the FP32 pipes.  GB300 runs FP64 FMAs at about 1/60 of the
+// FP32 rate, so the FP64 contractions use double-float arithmetic: every FP64
+// operand is split into hi + lo floats (48 significant bits), products are
+// formed exactly with an FMA (Dekker's product) plus the two cross terms,
+// and sums are error-free two-sums (Knuth) renormalized at every step, so a
+// partial sum carries about 2^-48 relative error per term -- the same order
+// as an FP64 dot product of the chunk lengths used here -- at roughly a
+// quarter of the FP32 rate instead of 1/60.
+struct DF {
+  float h, l;
+};
+// (the _rn intrinsics keep the compiler from contracting a product into a
+// following sum, which would break the exactness of the two-sums)
+__device__ __forceinline__ DF df_split(double v) {
+  const float h = __double2float_rn(v);
+  return DF{h, __double2float_rn(__dsub_rn(v, (double)h))};
+}
+// (sh, sl) += (ah + al) * (bh + bl), dropping al * bl
+__device__ __forceinline__ void df_fma(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float s = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  const float t = __fadd_rn(__fadd_rn(sl, err), e);
+  const float u = __fadd_rn(s, t);
+  sl = __fsub_rn(t, __fsub_rn(u, s));
+  sh = u;
+}
+
+// Partial Gram over one row chunk in double-float (layout as k_gram_partial)
+__global__ void __launch_bounds__(256) k_gram_partial_df(PairBlock<double> A, PairBlock<double> B,
+                                                         double* __restrict__ part) {
+  __shared__ float sAh[GK][GT + 4], sAl[GK][GT + 4];
+  __shared__ float sBh[GK][GT + 4], sBl[GK][GT + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
+  const long long r_begin = (long long)blockIdx.z * GROWS;
+  const long long r_end = min(A.n, r_begin + GROWS);
+  const int P2 = 2 * A.cols, Q2 = 2 * B.cols;
+  float ah_[4][4], al_[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) ah_[a][b] = al_[a][b] = 0.f;
+  for (long long r0 = r_begin; r0 < r_end; r0 += GK) {
+    for (int e = tid; e < GK * (GT / 2); e += 256) {
+      const int rr = e % GK, pp = e / GK;
+      const long long r = r0 + rr;
+      const int pa = i0 / 2 + pp, pb = j0 / 2 + pp;
+      double2 va = make_double2(0.0, 0.0), vb = make_double2(0.0, 0.0);
+      if (r < r_end && pa < A.cols) va = A.p[(long long)pa * A.ld + r];
+      if (r < r_end && pb < B.cols) vb = B.p[(long long)pb * B.ld + r];
+      DF t;
+      t = df_split(va.x); sAh[rr][2 * pp] = t.h; sAl[rr][2 * pp] = t.l;
+      t = df_split(va.y); sAh[rr][2 * pp + 1] = t.h; sAl[rr][2 * pp + 1] = t.l;
+      t = df_split(vb.x); sBh[rr][2 * pp] = t.h; sBl[rr][2 * pp] = t.l;
+      t = df_split(vb.y); sBh[rr][2 * pp + 1] = t.h; sBl[rr][2 * pp + 1] = t.l;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < GK; ++k) {
+      float xh[4], xl[4], yh[4], yl[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        xh[q] = sAh[k][4 * ty + q];
+        xl[q] = sAl[k][4 * ty + q];
+        yh[q] = sBh[k][4 * tx + q];
+        yl[q] = sBl[k][4 * tx + q];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) df_fma(ah_[p][q], al_[p][q], xh[p], xl[p], yh[q], yl[q]);
+    }
+    __syncthreads();
+  }
+  double* out = part + (long long)blockIdx.z * P2 * Q2;
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = i0 + 4 * ty + p, j = j0 + 4 * tx + q;
+      if (i < P2 && j < Q2) out[(long long)i * Q2 + j] = (double)ah_[p][q] + (double)al_[p][q];
+    }
+}
+
 __global__ void k_gram_reduce(const double* __restrict__ part, int nchunks, int nout,
                               double* __restrict__ G) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -115,6 +205,55 @@ __global__ void __launch_bounds__(256) k_update(PairBlock<R> A, const double* __
     if (beta != 0.0) {
       const T o = *yp;
       v = mk(fma((R)beta, o.x, v.x), fma((R)beta, o.y, v.y));
+    }
+    *yp = v;
+  }
+}
+
+// k_update for FP64 blocks in double-float (see df_fma)
+__global__ void __launch_bounds__(256) k_update_df(PairBlock<double> A, const double* __restrict__ C, int ldc,
+                                                   double beta, double2* __restrict__ Y, long long ldy, int Q,
+                                                   double alpha) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sCh = reinterpret_cast<float*>(smem_raw);  // [2P][UCOLS]
+  const int P2 = 2 * A.cols;
+  float* sCl = sCh + P2 * UCOLS;
+  const int j0 = blockIdx.y * UCOLS;
+  const int Q2 = 2 * Q;
+  for (int e = threadIdx.x; e < P2 * UCOLS; e += blockDim.x) {
+    const int k = e / UCOLS, j = e - k * UCOLS;
+    const DF t = df_split((j0 + j < Q2) ? alpha * C[(long long)k * ldc + j0 + j] : 0.0);
+    sCh[e] = t.h;
+    sCl[e] = t.l;
+  }
+  __syncthreads();
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= A.n) return;
+  float hh[UCOLS], ll[UCOLS];
+#pragma unroll
+  for (int j = 0; j < UCOLS; ++j) hh[j] = ll[j] = 0.f;
+  for (int p = 0; p < A.cols; ++p) {
+    const double2 a = A.p[(long long)p * A.ld + r];
+    const DF ax = df_split(a.x), ay = df_split(a.y);
+    const float* c0h = sCh + (2 * p) * UCOLS;
+    const float* c0l = sCl + (2 * p) * UCOLS;
+    const float* c1h = c0h + UCOLS;
+    const float* c1l = c0l + UCOLS;
+#pragma unroll
+    for (int j = 0; j < UCOLS; ++j) {
+      df_fma(hh[j], ll[j], ax.h, ax.l, c0h[j], c0l[j]);
+      df_fma(hh[j], ll[j], ay.h, ay.l, c1h[j], c1l[j]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < UCOLS / 2; ++q) {
+    const int qq = j0 / 2 + q;
+    if (qq >= Q) break;
+    double2* yp = Y + (long long)qq * ldy + r;
+    double2 v = make_double2((double)hh[2 * q] + (double)ll[2 * q], (double)hh[2 * q + 1] + (double)ll[2 * q + 1]);
+    if (beta != 0.0) {
+      const double2 o = *yp;
+      v = make_double2(fma(beta, o.x, v.x), fma(beta, o.y, v.y));
     }
     *yp = v;
   }
@@ -169,7 +308,11 @@ cudaError_t gram_pairs(const PairBlock<R>& A, const PairBlock<R>& B, double* G_d
   const long long nchunks = (A.n + GROWS - 1) / GROWS;
   if (ws_bytes < gram_workspace_bytes(A.cols, B.cols, A.n)) return cudaErrorInvalidValue;
   dim3 grid((P2 + GT - 1) / GT, (Q2 + GT - 1) / GT, (unsigned)nchunks);
-  k_gram_partial<R><<<grid, 256, 0, s>>>(A, B, (double*)ws);
+  if (sizeof(R) == 8)
+    k_gram_partial_df<<<grid, 256, 0, s>>>(*reinterpret_cast<const PairBlock<double>*>(&A),
+                                           *reinterpret_cast<const PairBlock<double>*>(&B), (double*)ws);
+  else
+    k_gram_partial<R><<<grid, 256, 0, s>>>(A, B, (double*)ws);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nout = P2 * Q2;
@@ -184,12 +327,20 @@ cudaError_t update_pairs(const PairBlock<R>& A, const double* C_dev, int ldc, do
   if (A.cols == 0) {
     return scale_pairs<R>(Y, ldy, A.n, Q, nullptr, beta, s);
   }
-  const size_t sm = sizeof(R) * (size_t)(2 * A.cols) * UCOLS;
+  const size_t sm = sizeof(R) * (size_t)(2 * A.cols) * UCOLS;   // double: hi + lo floats, same size
   if (sm > 200 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_update<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((A.n + 255) / 256), (unsigned)((2 * Q + UCOLS - 1) / UCOLS));
-  k_update<R><<<grid, 256, sm, s>>>(A, C_dev, ldc, beta, Y, ldy, Q, alpha);
+  cudaError_t e;
+  if (sizeof(R) == 8) {
+    e = cudaFuncSetAttribute(k_update_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_update_df<<<grid, 256, sm, s>>>(*reinterpret_cast<const PairBlock<double>*>(&A), C_dev, ldc, beta,
+                                      reinterpret_cast<double2*>(Y), ldy, Q, alpha);
+  } else {
+    e = cudaFuncSetAttribute(k_update<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_update<R><<<grid, 256, sm, s>>>(A, C_dev, ldc, beta, Y, ldy, Q, alpha);
+  }
   return cudaGetLastError();
 }
 
