@@ -140,11 +140,13 @@ APPLY_SOURCES = ["paper_2506_08308_gb300/csrc/apply_impl.cuh", "paper_2506_08308
 
 def apply_traffic():
     """DRAM bytes per call of the FP32 block product from the committed ncu
-    summary, or None when the kernels changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    summary (its TRAFFIC line), or None when the kernels changed since the
+    counters were taken."""
+    path = os.path.join(ROOT, "profiles", "bdg_apply_c64_2d_n256.md")
     try:
         with open(path) as f:
-            t = json.load(f)
+            line = next((x for x in f if x.startswith("TRAFFIC ")), None)
+        t = json.loads(line[len("TRAFFIC "):]) if line else {}
     except (OSError, ValueError):
         return None
     e = t.get("bdg_apply_c64_2d_n256")
