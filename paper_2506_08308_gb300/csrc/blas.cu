@@ -1,5 +1,7 @@
 // Tall-skinny block kernels (SIMT): pair Gram with FP64 cross-chunk
 // reduction, block update with FP64 coefficients, conversions.
+#include <algorithm>
+
 #include "blas.cuh"
 
 namespace bdg {
@@ -101,61 +103,104 @@ __device__ __forceinline__ void df_fma(float& sh, float& sl, float ah, float al,
   sh = u;
 }
 
-// Partial Gram over one row chunk in double-float (layout as k_gram_partial)
+// Partial Gram over one row chunk in double-float (layout as k_gram_partial),
+// output tile (16 MP) x (16 MQ) real columns so that narrow and 48-wide
+// blocks waste no arithmetic; with upper set (A and B tiled alike) only the
+// tiles on or above the diagonal are formed.
+template <int MP, int MQ>
 __global__ void __launch_bounds__(256) k_gram_partial_df(PairBlock<double> A, PairBlock<double> B,
-                                                         double* __restrict__ part) {
-  __shared__ float sAh[GK][GT + 4], sAl[GK][GT + 4];
-  __shared__ float sBh[GK][GT + 4], sBl[GK][GT + 4];
+                                                         double* __restrict__ part, int upper) {
+  constexpr int TP = 16 * MP, TQ = 16 * MQ;
+  if (upper && blockIdx.y < blockIdx.x) return;
+  __shared__ float sAh[GK][TP + 4], sAl[GK][TP + 4];
+  __shared__ float sBh[GK][TQ + 4], sBl[GK][TQ + 4];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
+  const int i0 = blockIdx.x * TP, j0 = blockIdx.y * TQ;
   const long long r_begin = (long long)blockIdx.z * GROWS;
   const long long r_end = min(A.n, r_begin + GROWS);
   const int P2 = 2 * A.cols, Q2 = 2 * B.cols;
-  float ah_[4][4], al_[4][4];
+  float ah_[MP][MQ], al_[MP][MQ];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < MP; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) ah_[a][b] = al_[a][b] = 0.f;
+    for (int b = 0; b < MQ; ++b) ah_[a][b] = al_[a][b] = 0.f;
   for (long long r0 = r_begin; r0 < r_end; r0 += GK) {
-    for (int e = tid; e < GK * (GT / 2); e += 256) {
+    for (int e = tid; e < GK * (TP / 2); e += 256) {
       const int rr = e % GK, pp = e / GK;
       const long long r = r0 + rr;
-      const int pa = i0 / 2 + pp, pb = j0 / 2 + pp;
-      double2 va = make_double2(0.0, 0.0), vb = make_double2(0.0, 0.0);
+      const int pa = i0 / 2 + pp;
+      double2 va = make_double2(0.0, 0.0);
       if (r < r_end && pa < A.cols) va = A.p[(long long)pa * A.ld + r];
-      if (r < r_end && pb < B.cols) vb = B.p[(long long)pb * B.ld + r];
       DF t;
       t = df_split(va.x); sAh[rr][2 * pp] = t.h; sAl[rr][2 * pp] = t.l;
       t = df_split(va.y); sAh[rr][2 * pp + 1] = t.h; sAl[rr][2 * pp + 1] = t.l;
+    }
+    for (int e = tid; e < GK * (TQ / 2); e += 256) {
+      const int rr = e % GK, pp = e / GK;
+      const long long r = r0 + rr;
+      const int pb = j0 / 2 + pp;
+      double2 vb = make_double2(0.0, 0.0);
+      if (r < r_end && pb < B.cols) vb = B.p[(long long)pb * B.ld + r];
+      DF t;
       t = df_split(vb.x); sBh[rr][2 * pp] = t.h; sBl[rr][2 * pp] = t.l;
       t = df_split(vb.y); sBh[rr][2 * pp + 1] = t.h; sBl[rr][2 * pp + 1] = t.l;
     }
     __syncthreads();
 #pragma unroll 4
     for (int k = 0; k < GK; ++k) {
-      float xh[4], xl[4], yh[4], yl[4];
+      float xh[MP], xl[MP], yh[MQ], yl[MQ];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        xh[q] = sAh[k][4 * ty + q];
-        xl[q] = sAl[k][4 * ty + q];
-        yh[q] = sBh[k][4 * tx + q];
-        yl[q] = sBl[k][4 * tx + q];
+      for (int q = 0; q < MP; ++q) {
+        xh[q] = sAh[k][MP * ty + q];
+        xl[q] = sAl[k][MP * ty + q];
       }
 #pragma unroll
-      for (int p = 0; p < 4; ++p)
+      for (int q = 0; q < MQ; ++q) {
+        yh[q] = sBh[k][MQ * tx + q];
+        yl[q] = sBl[k][MQ * tx + q];
+      }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) df_fma(ah_[p][q], al_[p][q], xh[p], xl[p], yh[q], yl[q]);
+      for (int p = 0; p < MP; ++p)
+#pragma unroll
+        for (int q = 0; q < MQ; ++q) df_fma(ah_[p][q], al_[p][q], xh[p], xl[p], yh[q], yl[q]);
     }
     __syncthreads();
   }
   double* out = part + (long long)blockIdx.z * P2 * Q2;
 #pragma unroll
-  for (int p = 0; p < 4; ++p)
+  for (int p = 0; p < MP; ++p)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = i0 + 4 * ty + p, j = j0 + 4 * tx + q;
+    for (int q = 0; q < MQ; ++q) {
+      const int i = i0 + MP * ty + p, j = j0 + MQ * tx + q;
       if (i < P2 && j < Q2) out[(long long)i * Q2 + j] = (double)ah_[p][q] + (double)al_[p][q];
     }
+}
+
+// tile multiple m (tile 16 m) for n real columns: least padded work, then the larger tile
+inline int tile_mult(int n) {
+  int best = 4;
+  long long bw = -1;
+  for (int m = 4; m >= 1; --m) {
+    const long long w = (long long)((n + 16 * m - 1) / (16 * m)) * 16 * m;
+    if (bw < 0 || w < bw) {
+      bw = w;
+      best = m;
+    }
+  }
+  return best;
+}
+
+// G = sum over chunks; with tile > 0, entries below the diagonal tiles are
+// read from their mirror (upper-triangle Grams)
+__global__ void k_gram_reduce_upper(const double* __restrict__ part, int nchunks, int P2, int Q2, int tile,
+                                    double* __restrict__ G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= P2 * Q2) return;
+  const int i = e / Q2, j = e - i * Q2;
+  const int src = (i / tile > j / tile) ? j * Q2 + i : e;
+  double s = 0.0;
+  for (int c = 0; c < nchunks; ++c) s += part[(long long)c * P2 * Q2 + src];
+  G[e] = s;
 }
 
 __global__ void k_gram_reduce(const double* __restrict__ part, int nchunks, int nout,
@@ -300,7 +345,7 @@ size_t gram_workspace_bytes(int P, int Q, long long n) {
 
 template <typename R>
 cudaError_t gram_pairs(const PairBlock<R>& A, const PairBlock<R>& B, double* G_dev, void* ws,
-                       size_t ws_bytes, cudaStream_t s) {
+                       size_t ws_bytes, cudaStream_t s, bool upper) {
   if (A.n != B.n) return cudaErrorInvalidValue;
   const int P2 = 2 * A.cols, Q2 = 2 * B.cols;
   if (P2 == 0 || Q2 == 0) return cudaSuccess;
@@ -308,11 +353,28 @@ cudaError_t gram_pairs(const PairBlock<R>& A, const PairBlock<R>& B, double* G_d
   const long long nchunks = (A.n + GROWS - 1) / GROWS;
   if (ws_bytes < gram_workspace_bytes(A.cols, B.cols, A.n)) return cudaErrorInvalidValue;
   dim3 grid((P2 + GT - 1) / GT, (Q2 + GT - 1) / GT, (unsigned)nchunks);
-  if (sizeof(R) == 8)
-    k_gram_partial_df<<<grid, 256, 0, s>>>(*reinterpret_cast<const PairBlock<double>*>(&A),
-                                           *reinterpret_cast<const PairBlock<double>*>(&B), (double*)ws);
-  else
-    k_gram_partial<R><<<grid, 256, 0, s>>>(A, B, (double*)ws);
+  if (sizeof(R) == 8) {
+    const PairBlock<double>& A8 = *reinterpret_cast<const PairBlock<double>*>(&A);
+    const PairBlock<double>& B8 = *reinterpret_cast<const PairBlock<double>*>(&B);
+    int mp = tile_mult(P2), mq = tile_mult(Q2);
+    const bool up = upper && P2 == Q2;
+    if (up) mp = mq = std::max(mp, mq);
+    dim3 g8((P2 + 16 * mp - 1) / (16 * mp), (Q2 + 16 * mq - 1) / (16 * mq), (unsigned)nchunks);
+#define BDG_GDF(MP_, MQ_) \
+  if (mp == MP_ && mq == MQ_) k_gram_partial_df<MP_, MQ_><<<g8, 256, 0, s>>>(A8, B8, (double*)ws, up ? 1 : 0);
+    BDG_GDF(1, 1) BDG_GDF(1, 2) BDG_GDF(1, 3) BDG_GDF(1, 4)
+    BDG_GDF(2, 1) BDG_GDF(2, 2) BDG_GDF(2, 3) BDG_GDF(2, 4)
+    BDG_GDF(3, 1) BDG_GDF(3, 2) BDG_GDF(3, 3) BDG_GDF(3, 4)
+    BDG_GDF(4, 1) BDG_GDF(4, 2) BDG_GDF(4, 3) BDG_GDF(4, 4)
+#undef BDG_GDF
+    cudaError_t e8 = cudaGetLastError();
+    if (e8 != cudaSuccess) return e8;
+    const int nout8 = P2 * Q2;
+    k_gram_reduce_upper<<<(nout8 + 255) / 256, 256, 0, s>>>((const double*)ws, (int)nchunks, P2, Q2,
+                                                            up ? 16 * mp : (1 << 30), G_dev);
+    return cudaGetLastError();
+  }
+  k_gram_partial<R><<<grid, 256, 0, s>>>(A, B, (double*)ws);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nout = P2 * Q2;
@@ -361,9 +423,9 @@ cudaError_t scale_pairs(typename CT<R>::T* Y, long long ldy, long long n, int co
 }
 
 template cudaError_t gram_pairs<float>(const PairBlock<float>&, const PairBlock<float>&, double*,
-                                       void*, size_t, cudaStream_t);
+                                       void*, size_t, cudaStream_t, bool);
 template cudaError_t gram_pairs<double>(const PairBlock<double>&, const PairBlock<double>&, double*,
-                                        void*, size_t, cudaStream_t);
+                                        void*, size_t, cudaStream_t, bool);
 template cudaError_t update_pairs<float>(const PairBlock<float>&, const double*, int, double,
                                          float2*, long long, int, cudaStream_t, double);
 template cudaError_t update_pairs<double>(const PairBlock<double>&, const double*, int, double,

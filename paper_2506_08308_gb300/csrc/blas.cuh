@@ -21,11 +21,13 @@ struct PairBlock {
 };
 
 // G (2P x 2Q, row-major, FP64) = A^T B over real columns; partial sums per
-// row chunk are accumulated in R and reduced across chunks in FP64.
-// ws must hold gram_workspace_bytes(P, Q, n) bytes.
+// row chunk are accumulated in R (FP64 blocks: double-float) and reduced
+// across chunks in FP64.  ws must hold gram_workspace_bytes(P, Q, n) bytes.
+// upper (FP64 blocks with P == Q): G is known to be symmetric; only the
+// tiles on and above the diagonal are formed and the rest mirrored.
 template <typename R>
 cudaError_t gram_pairs(const PairBlock<R>& A, const PairBlock<R>& B, double* G_dev, void* ws,
-                       size_t ws_bytes, cudaStream_t s);
+                       size_t ws_bytes, cudaStream_t s, bool upper = false);
 size_t gram_workspace_bytes(int P, int Q, long long n);
 
 // Y[:, q].t = beta * Y[:, q].t + alpha * sum_{p,s} A[:, p].s * C[(2p+s) * ldc + 2q+t]

@@ -272,8 +272,8 @@ class Solver {
 
   // ---- primitive wrappers ----------------------------------------------
   // G (2P x 2Q) of real columns, FP64 on device
-  bdg_status gram(const PairBlock<R>& A, const PairBlock<R>& B, double* G) {
-    BDG_CUDA_TRY(plan_, gram_pairs<R>(A, B, G, gws_, gws_bytes_, s_));
+  bdg_status gram(const PairBlock<R>& A, const PairBlock<R>& B, double* G, bool upper = false) {
+    BDG_CUDA_TRY(plan_, gram_pairs<R>(A, B, G, gws_, gws_bytes_, s_, upper));
     return BDG_OK;
   }
   // Y (Q pairs at y) = beta Y + A C with C on the device (2P rows used, ldc)
