@@ -682,12 +682,9 @@ class Solver {
       const int nxt = 1 - cur_;
       const double* Pc = dmat_[MAT_P];
       const double* Qc = dmat_[MAT_Q];
-      // new Ritz block into the other bank
-      if ((st = update_dev(fpart(U_[cur_], 0, pu), Pc, ldc, 0.0, fptr(U_[nxt], 0), mmp))) return st;
-      if ((st = update_dev(gpart(U_[cur_], 0, pu), Qc, ldc, 0.0, gptr(U_[nxt], 0), mmp))) return st;
-      if ((st = update_dev(fpart(HU_[cur_], 0, pu), Pc, ldc, 0.0, fptr(HU_[nxt], 0), mmp))) return st;
-      if ((st = update_dev(gpart(HU_[cur_], 0, pu), Qc, ldc, 0.0, gptr(HU_[nxt], 0), mmp))) return st;
-      // previous update P: the [D P]-part of the basis times its coefficient rows
+      // previous update P: the [D P]-part of the basis times its coefficient
+      // rows; the new Ritz block is then X-part + P, which spares the [D P]
+      // columns a second pass
       bool haveP = nxb > 0 && nu > nxb;
       if (haveP) {
         const int p0 = nxb / 2, pp = pu - p0;
@@ -697,6 +694,19 @@ class Solver {
         if ((st = update_dev(gpart(U_[cur_], p0, pp), Qd, ldc, 0.0, gptr(Pb_, 0), mmp))) return st;
         if ((st = update_dev(fpart(HU_[cur_], p0, pp), Pd, ldc, 0.0, fptr(HPb_, 0), mmp))) return st;
         if ((st = update_dev(gpart(HU_[cur_], p0, pp), Qd, ldc, 0.0, gptr(HPb_, 0), mmp))) return st;
+        const size_t bytes = sizeof(T) * (size_t)vlen_ * mmp;
+        BDG_CUDA_TRY(plan_, cudaMemcpyAsync(U_[nxt], Pb_, bytes, cudaMemcpyDeviceToDevice, s_));
+        BDG_CUDA_TRY(plan_, cudaMemcpyAsync(HU_[nxt], HPb_, bytes, cudaMemcpyDeviceToDevice, s_));
+        if ((st = update_dev(fpart(U_[cur_], 0, p0), Pc, ldc, 1.0, fptr(U_[nxt], 0), mmp))) return st;
+        if ((st = update_dev(gpart(U_[cur_], 0, p0), Qc, ldc, 1.0, gptr(U_[nxt], 0), mmp))) return st;
+        if ((st = update_dev(fpart(HU_[cur_], 0, p0), Pc, ldc, 1.0, fptr(HU_[nxt], 0), mmp))) return st;
+        if ((st = update_dev(gpart(HU_[cur_], 0, p0), Qc, ldc, 1.0, gptr(HU_[nxt], 0), mmp))) return st;
+      } else {
+        // new Ritz block into the other bank
+        if ((st = update_dev(fpart(U_[cur_], 0, pu), Pc, ldc, 0.0, fptr(U_[nxt], 0), mmp))) return st;
+        if ((st = update_dev(gpart(U_[cur_], 0, pu), Qc, ldc, 0.0, gptr(U_[nxt], 0), mmp))) return st;
+        if ((st = update_dev(fpart(HU_[cur_], 0, pu), Pc, ldc, 0.0, fptr(HU_[nxt], 0), mmp))) return st;
+        if ((st = update_dev(gpart(HU_[cur_], 0, pu), Qc, ldc, 0.0, gptr(HU_[nxt], 0), mmp))) return st;
       }
       if (dbg_ && haveP) fprintf(stderr, "[bdg]   dbg P images after extraction %.3e\n", dbg_img(Pb_, HPb_, mmp));
       cur_ = nxt;
