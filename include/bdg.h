@@ -121,7 +121,9 @@ bdg_status bdg_apply(bdg_plan_t plan, int mode, int dtype, const void* x, void* 
  *   F <- F X Sigma^-1/2,  G <- G Y Sigma^-1/2,
  * with rtol = 1e-12 (C128) or 1e-6 (C64).  The first *rank columns of F and G
  * hold the result; the rest are zeroed.  Gram entries are accumulated in
- * FP64.  Returns BDG_ERR_BREAKDOWN (with *rank = 0) if S is zero.
+ * FP64; the SVD comes from the Hermitian matrix [[0, S], [S^H, 0]].
+ * Limits: ncol <= 40, nlock <= 256 (BDG_ERR_UNSUPPORTED beyond).  F and G
+ * must not overlap.  Returns BDG_ERR_BREAKDOWN (with *rank = 0) if S is zero.
  */
 bdg_status bdg_biortho(bdg_plan_t plan, int dtype, void* F, void* G, int ncol, const void* Fl,
                        const void* Gl, int nlock, int* rank, void* stream);

@@ -1,4 +1,4 @@
-// bdg_solve / bdg_biortho: the structure-preserving subspace iteration for
+// bdg_solve: the structure-preserving subspace iteration for
 // the k smallest positive excitations (Sections 2.2-2.3, 3.1-3.2).
 //
 // The operator is real for a real ground state (Section 2.2), so the
@@ -1086,10 +1086,5 @@ bdg_status bdg_solve(bdg_plan_t plan, int k, int m, const void* X0, double* omeg
   if (nc < k) return fail(plan, BDG_ERR_NOT_CONVERGED, "not converged within maxit");
   return BDG_OK;
 }
-
-bdg_status bdg_biortho(bdg_plan_t plan, int, void*, void*, int, const void*, const void*, int, int*, void*) {
-  return fail(plan, BDG_ERR_UNSUPPORTED, "bdg_biortho not built yet");
-}
-
 
 }  // extern "C"
