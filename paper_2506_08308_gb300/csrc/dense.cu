@@ -120,29 +120,33 @@ __global__ void __launch_bounds__(1024) k_jacobi(int n, const double* __restrict
         cs[2 * k + 1] = s;
       }
       __syncthreads();
-      // rows: (row_p, row_q) <- (c row_p - s row_q, s row_p + c row_q)
-      for (int e = tid; e < npair * n; e += nt) {
-        const int k = e / n, j = e - k * n;
-        const int p = pq[2 * k], q = pq[2 * k + 1];
-        if (p == q) continue;
-        const float c = cs[2 * k], s = cs[2 * k + 1];
-        const float ap = A[p * ld + j], aq = A[q * ld + j];
-        A[p * ld + j] = c * ap - s * aq;
-        A[q * ld + j] = s * ap + c * aq;
-      }
-      __syncthreads();
-      // columns of A and V
-      for (int e = tid; e < npair * n; e += nt) {
-        const int k = e / n, i = e - k * n;
-        const int p = pq[2 * k], q = pq[2 * k + 1];
-        if (p == q) continue;
-        const float c = cs[2 * k], s = cs[2 * k + 1];
-        const float ap = A[i * ld + p], aq = A[i * ld + q];
-        A[i * ld + p] = c * ap - s * aq;
-        A[i * ld + q] = s * ap + c * aq;
-        const float vp = V[i * ld + p], vq = V[i * ld + q];
-        V[i * ld + p] = c * vp - s * vq;
-        V[i * ld + q] = s * vp + c * vq;
+      // A <- J^T A J and V <- V J in one pass: a work item is the 2 x 2 block
+      // (row pair k, column pair l) of A -- rows first, then columns, as the
+      // two one-sided updates would do -- or a row of V's column pair l.  A
+      // dummy pair (odd n) has p == q and c = 1, s = 0, which makes its
+      // duplicate reads and writes agree.
+      const int nblk = npair * npair;
+      for (int e = tid; e < nblk + npair * n; e += nt) {
+        if (e < nblk) {
+          const int k = e / npair, l = e - k * npair;
+          const int p = pq[2 * k], q = pq[2 * k + 1], u = pq[2 * l], v = pq[2 * l + 1];
+          const float ck = cs[2 * k], sk = cs[2 * k + 1], cl = cs[2 * l], sl = cs[2 * l + 1];
+          const float x00 = A[p * ld + u], x01 = A[p * ld + v], x10 = A[q * ld + u], x11 = A[q * ld + v];
+          const float r00 = ck * x00 - sk * x10, r01 = ck * x01 - sk * x11;
+          const float r10 = sk * x00 + ck * x10, r11 = sk * x01 + ck * x11;
+          A[p * ld + u] = cl * r00 - sl * r01;
+          A[p * ld + v] = sl * r00 + cl * r01;
+          A[q * ld + u] = cl * r10 - sl * r11;
+          A[q * ld + v] = sl * r10 + cl * r11;
+        } else {
+          const int f = e - nblk, l = f / n, i = f - l * n;
+          const int u = pq[2 * l], v = pq[2 * l + 1];
+          if (u == v) continue;
+          const float cl = cs[2 * l], sl = cs[2 * l + 1];
+          const float vp = V[i * ld + u], vq = V[i * ld + v];
+          V[i * ld + u] = cl * vp - sl * vq;
+          V[i * ld + v] = sl * vp + cl * vq;
+        }
       }
       __syncthreads();
     }
