@@ -38,7 +38,7 @@ W = synth.CONFIG2
 TOL = 1e-10
 # Iterations the block solver needs on this workload (the device mixed solve
 # from the seeded start block); the CPU timings are extrapolated to it.
-SOLVE_ITERATIONS = 165
+SOLVE_ITERATIONS = 170
 
 
 def parse():
