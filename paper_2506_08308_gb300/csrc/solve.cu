@@ -1059,7 +1059,7 @@ bdg_status bdg_solve(bdg_plan_t plan, int k, int m, const void* X0, double* omeg
   int it1 = 0, it2 = 0;
   Solver<double> S64(plan, s, m);
   S64.sigma_ = sigma;
-  S64.rtol_ = 1e-8;
+  S64.rtol_ = 1e-5;
   if (plan->prm.prec == BDG_MIXED) {
     Solver<float> S32(plan, s, m);
     S32.sigma_ = sigma;
