@@ -668,8 +668,6 @@ class Solver {
     int stall = 0;
     bool refresh_next = false;
     int refreshed_at = -1;
-    double best64 = INFINITY;
-    int stall64 = 0;
     for (int it = 0; it < maxit; ++it) {
       plan_->stats.iterations++;
       if (sizeof(R) == 4) plan_->stats.iterations_fp32++;
@@ -714,7 +712,9 @@ class Solver {
       T* HX = HU_[cur_];
       // The images HX are carried by linear combination; their rounding
       // drifts slowly away from H X.  Recompute them exactly every 20
-      // iterations, after a stall, and before a convergence claim is accepted.
+      // iterations and before a convergence claim is accepted.  (A refresh
+      // on every stall dropped the previous-update block P again and again
+      // near the floor and could keep the iteration from recovering.)
       const bool refresh = refresh_next || (it > 0 && it % 20 == 0);
       if (refresh) {
         if ((st = apply_fg(X, HX, mmp))) return st;
@@ -780,16 +780,6 @@ class Solver {
       if (mm >= k && nconv == k) {
         *converged = true;
         return BDG_OK;
-      }
-      if (stop_floor == 0) {  // FP64 phase: a stall triggers exact images
-        if (worst < 0.9 * best64) {
-          best64 = worst;
-          stall64 = 0;
-        } else if (++stall64 >= 5) {
-          refresh_next = true;
-          stall64 = 0;
-          best64 = worst;
-        }
       }
       if (stop_floor > 0) {
         if (mm >= k && worst < stop_floor) return BDG_OK;
