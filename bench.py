@@ -66,6 +66,27 @@ def dist_env():
     return world, rank, local
 
 
+def rank_barrier(dist):
+    """Barrier over the ranks (no-op on one process)."""
+    if dist is not None:
+        dist.barrier()
+
+
+def reduce_max(dist, x, device):
+    """Maximum of x over the ranks (the timing of the slowest rank)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def instance_seed(w, rank):
+    """Start-block seed of rank's independent instance (weak scaling)."""
+    return w.block_seed + 7919 * rank
+
+
 class ClockSampler:
     """nvidia-smi samples (every 200 ms) while the timed region runs."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -277,22 +298,17 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        rank_barrier(dist)
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(dist, x, dev)
 
     # ---- inputs (untimed): ground state on the device, seeded start block
     w = W
     V = synth.potential(w)
     phi, mu, gres, git = bdg.ground_state(bdg.params_from(w), w.M, V, synth.initial_spinor(w), tol=1e-12)
-    seed = w.block_seed + 7919 * rank          # an independent instance per rank
+    seed = instance_seed(w, rank)              # an independent instance per rank
     X0h = synth.random_block(w, w.m, complex_=True, seed=seed)
     X0 = torch.from_numpy(X0h).to(dev)
     plan = bdg.Plan(bdg.params_from(w, prec=bdg.MIXED, tol=TOL, maxit=3000), V, phi.reshape(-1))
