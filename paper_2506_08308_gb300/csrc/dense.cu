@@ -348,7 +348,13 @@ cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double
     int i1 = i0 + 1;
     while (i1 < n && hw[i1] - hw[i1 - 1] < tau) ++i1;
     const int ns = i1 - i0;
-    if (ns >= 2 && hw[i1 - 1] > hw[i0]) {
+    // a run whose spread is at the FP64 rounding level -- of its own values
+    // or of the whole matrix -- is degenerate to working precision: any
+    // orthonormal basis of it is an eigenbasis and nothing is re-solved
+    const double spread = hw[i1 - 1] - hw[i0];
+    const double mag = std::max(std::fabs(hw[i0]), std::fabs(hw[i1 - 1]));
+    const bool degenerate = spread <= 1e-12 * mag || spread <= 64 * 2.220446049250313e-16 * amax;
+    if (ns >= 2 && spread > 0 && !degenerate) {
       const double c = 0.5 * (hw[i0] + hw[i1 - 1]);  // midpoint: the shifted norm is half the spread
       double* Vs = ws;                         // n x ns
       double* AVs = Vs + (size_t)n * ns;       // n x ns
