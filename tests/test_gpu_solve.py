@@ -3,7 +3,7 @@ eq. lrep-d: the k smallest positive excitations to 1e-10 relative, the
 amplitudes per degenerate cluster to 1e-8 (projector metric of Section 4.1),
 residuals <= 1e-10 in FP64, and the normalization / bi-orthogonality
 h^d (u_i.u_j - v_i.v_j) = delta_ij (eq. constrain, Theorem
-"Biorthogonality"); FP64 and mixed precision, 1-D and 2-D, odd and even
+"Biorthogonality"); FP64 and mixed precision, 1-D, 2-D and 3-D, odd and even
 block sizes, a start block passed in and the internal seeded one."""
 import numpy as np
 import pytest
@@ -19,6 +19,8 @@ W1Q = synth.Workload("s1d_n64_q", (64,), (-8.0,), (8.0,), (1.0,), 10.0, -1.0, 0.
                      gs_seed=102, block_seed=9)
 W2 = synth.Workload("s2d_16", (16, 16), (-6.0, -6.0), (6.0, 6.0), (1.0, 1.4), 12.0, -1.0, 0.05, 0.3, k=10, m=14,
                     gs_seed=8, block_seed=3)
+W3 = synth.Workload("s3d_8", (8, 8, 8), (-4.0,) * 3, (4.0,) * 3, (1.0, 1.2, 1.5), 8.0, -0.5, 0.02, 0.2, k=6,
+                    m=10, gs_seed=31, block_seed=32)
 WC1 = synth.CONFIG1
 
 
@@ -56,7 +58,7 @@ def _check(w, op, om, UV, resid, k, dense):
     assert r.max() < 1e-9, r
 
 
-@pytest.mark.parametrize("w", [W1, W1Q, W2], ids=lambda w: w.name)
+@pytest.mark.parametrize("w", [W1, W1Q, W2, W3], ids=lambda w: w.name)
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_solve_matches_dense(w, prec):
     torch = need_torch_cuda()
