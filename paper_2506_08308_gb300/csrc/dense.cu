@@ -329,7 +329,7 @@ namespace {
 // whose norm is about the spread, and rotated back.  Runs are disjoint, so
 // the workspace is reused from one to the next.
 cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double* V, double* ws, int depth,
-                              cudaStream_t s) {
+                              double floor, double shift, cudaStream_t s) {
   const size_t sm = sizeof(float) * (2 * (size_t)n * (n + 1) + 2 * (n / 2 + 1)) +
                     sizeof(int) * 2 * (n / 2 + 1) + sizeof(float) * 64;
   cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -343,6 +343,7 @@ cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double
   double amax = 0.0;
   for (double v : hw) amax = std::max(amax, std::fabs(v));
   if (!(amax > 0)) return cudaSuccess;
+  if (depth == 0) floor *= amax;   // the caller's floor is relative at the top level
   const double tau = 1e-4 * amax;
   for (int i0 = 0; i0 < n;) {
     int i1 = i0 + 1;
@@ -354,7 +355,10 @@ cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double
     const double spread = hw[i1 - 1] - hw[i0];
     const double mag = std::max(std::fabs(hw[i0]), std::fabs(hw[i1 - 1]));
     const bool degenerate = spread <= 1e-12 * mag || spread <= 64 * 2.220446049250313e-16 * amax;
-    if (ns >= 2 && spread > 0 && !degenerate) {
+    // runs whose eigenvalues all lie below the caller's floor (|lambda| of the
+    // original matrix) are not needed resolved: the caller discards them
+    const double top = std::max(std::fabs(hw[i0] + shift), std::fabs(hw[i1 - 1] + shift));
+    if (ns >= 2 && spread > 0 && !degenerate && !(top < floor)) {
       const double c = 0.5 * (hw[i0] + hw[i1 - 1]);  // midpoint: the shifted norm is half the spread
       double* Vs = ws;                         // n x ns
       double* AVs = Vs + (size_t)n * ns;       // n x ns
@@ -382,7 +386,7 @@ cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double
       if ((e = dsym_small(ns, As, ns, s))) return e;
       k_add_diag<<<(ns + 127) / 128, 128, 0, s>>>(ns, As, ns, -c);
       if ((e = cudaGetLastError())) return e;
-      if ((e = jacobi_multilevel(ns, As, ns, w2, V2, rest, depth + 1, s))) return e;
+      if ((e = jacobi_multilevel(ns, As, ns, w2, V2, rest, depth + 1, floor, shift + c, s))) return e;
       k_add_vec<<<(ns + 127) / 128, 128, 0, s>>>(ns, w2, c);
       if ((e = cudaGetLastError())) return e;
       if ((e = dgemm_small(false, false, n, ns, ns, 1.0, Vs, ns, V2, ns, 0.0, Vn, ns, s))) return e;
@@ -399,7 +403,7 @@ cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double
 }  // namespace
 
 cudaError_t eigh(int n, const double* A, int lda, double* w, double* V, double* ws, int refine_steps,
-                 cudaStream_t s) {
+                 cudaStream_t s, double floor_rel) {
   if (n <= 0) return cudaSuccess;
   if (n > SMALL_MAX) return cudaErrorInvalidValue;
   cudaError_t e;
@@ -412,7 +416,7 @@ cudaError_t eigh(int n, const double* A, int lda, double* w, double* V, double* 
   double* lam2 = lam + n;         // n
   double* anorm = lam2 + n;       // 8
   double* rest = anorm + 8;
-  if ((e = jacobi_multilevel(n, A, lda, lam2, X, rest, 0, s))) return e;
+  if ((e = jacobi_multilevel(n, A, lda, lam2, X, rest, 0, floor_rel, 0.0, s))) return e;
   k_frob<<<1, 1024, 0, s>>>(n, A, lda, anorm);
   double* cur = X;
   double* nxt = X2;

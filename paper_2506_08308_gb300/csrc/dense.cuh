@@ -20,8 +20,11 @@ cudaError_t dgemm_small(bool ta, bool tb, int m, int n, int k, double alpha, con
 // decomposition") bring it to FP64 accuracy.  ws: workspace of
 // eigh_workspace_doubles(n) doubles.  V is n x n row-major (ld n).
 size_t eigh_workspace_doubles(int n);
+// floor_rel > 0: eigenvalues with |lambda| < floor_rel max|lambda| are
+// returned orthonormal but not resolved from each other (for callers that
+// discard them).
 cudaError_t eigh(int n, const double* A, int lda, double* w, double* V, double* ws, int refine_steps,
-                 cudaStream_t s);
+                 cudaStream_t s, double floor_rel = 0.0);
 
 // Elementwise helpers on small matrices (row-major).
 // B[i][j] = A[i][j] * dl[i] * dr[j]  (dl / dr may be NULL = ones)

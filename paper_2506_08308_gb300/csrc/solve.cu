@@ -340,9 +340,10 @@ class Solver {
   }
   // symmetric eigen-decomposition of the n x n device matrix A (ld lda),
   // ascending w to the host, V to dV (n x n, ld n)
-  bdg_status eigh_dev(int n, const double* A, int lda, double* dw, double* dV, std::vector<double>& w) {
+  bdg_status eigh_dev(int n, const double* A, int lda, double* dw, double* dV, std::vector<double>& w,
+                      double floor_rel = 0.0) {
     if (n > SMALL_MAX) return fail(plan_, BDG_ERR_UNSUPPORTED, "projected problem larger than supported");
-    bdg_status st = cuda(eigh(n, A, lda, dw, dV, dws_, 3, s_), "eigh");
+    bdg_status st = cuda(eigh(n, A, lda, dw, dV, dws_, 3, s_, floor_rel), "eigh");
     if (st) return st;
     if ((st = download(dw, w, n))) return st;
     if (dbg_eigh_) check_eigh(n, A, lda, dV, w);
@@ -456,7 +457,7 @@ class Solver {
     k_jordan_wielandt<<<(n2 * n2 + 255) / 256, 256, 0, s_>>>(ncols, S, ld, J);
     BDG_CUDA_TRY(plan_, cudaGetLastError());
     std::vector<double> w;
-    if ((st = eigh_dev(n2, J, n2, dvec_, Vj, w))) return st;
+    if ((st = eigh_dev(n2, J, n2, dvec_, Vj, w, 0.1 * rtol))) return st;   // sigma < rtol sigma_max is dropped
     const double smax = std::max(w[n2 - 1], 0.0);
     if (log_)
       fprintf(stderr, "[bdg]   biortho ncols %d sigma [%.3e, %.3e]", ncols, std::max(w[ncols], 0.0), smax);
@@ -517,7 +518,7 @@ class Solver {
       ldt = n;
     }
     std::vector<double> lam;
-    bdg_status st = eigh_dev(n, Kt, ldt, dvec_, Q, lam);
+    bdg_status st = eigh_dev(n, Kt, ldt, dvec_, Q, lam, 1e-11);   // lam <= 1e-10 lam_max is cut
     if (st) return st;
     const double lmax = lam[n - 1];
     if (!(lmax > 0)) return fail(plan_, BDG_ERR_BREAKDOWN, "projected H_+ is not positive");
