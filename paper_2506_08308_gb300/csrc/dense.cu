@@ -402,8 +402,18 @@ cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double
 
 }  // namespace
 
+// X = I, lam = diag(A): the start for nearly diagonal matrices
+__global__ void k_identity_start(int n, const double* __restrict__ A, int lda, double* __restrict__ X,
+                                 double* __restrict__ lam) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+    const int i = e / n, j = e - i * n;
+    X[e] = i == j ? 1.0 : 0.0;
+    if (i == j) lam[i] = A[(long long)i * lda + i];
+  }
+}
+
 cudaError_t eigh(int n, const double* A, int lda, double* w, double* V, double* ws, int refine_steps,
-                 cudaStream_t s, double floor_rel) {
+                 cudaStream_t s, double floor_rel, bool from_identity) {
   if (n <= 0) return cudaSuccess;
   if (n > SMALL_MAX) return cudaErrorInvalidValue;
   cudaError_t e;
@@ -416,7 +426,12 @@ cudaError_t eigh(int n, const double* A, int lda, double* w, double* V, double* 
   double* lam2 = lam + n;         // n
   double* anorm = lam2 + n;       // 8
   double* rest = anorm + 8;
-  if ((e = jacobi_multilevel(n, A, lda, lam2, X, rest, 0, floor_rel, 0.0, s))) return e;
+  if (from_identity) {
+    k_identity_start<<<(n * n + 255) / 256, 256, 0, s>>>(n, A, lda, X, lam2);
+    if ((e = cudaGetLastError())) return e;
+  } else if ((e = jacobi_multilevel(n, A, lda, lam2, X, rest, 0, floor_rel, 0.0, s))) {
+    return e;
+  }
   k_frob<<<1, 1024, 0, s>>>(n, A, lda, anorm);
   double* cur = X;
   double* nxt = X2;

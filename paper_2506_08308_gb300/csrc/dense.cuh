@@ -22,9 +22,12 @@ cudaError_t dgemm_small(bool ta, bool tb, int m, int n, int k, double alpha, con
 size_t eigh_workspace_doubles(int n);
 // floor_rel > 0: eigenvalues with |lambda| < floor_rel max|lambda| are
 // returned orthonormal but not resolved from each other (for callers that
-// discard them).
+// discard them).  from_identity: start the refinement from V = I instead of
+// the Jacobi basis, for matrices that are diagonal up to small off-diagonal
+// entries (the refinement then resolves every pair whose gap exceeds a
+// hundred times its coupling).
 cudaError_t eigh(int n, const double* A, int lda, double* w, double* V, double* ws, int refine_steps,
-                 cudaStream_t s, double floor_rel = 0.0);
+                 cudaStream_t s, double floor_rel = 0.0, bool from_identity = false);
 
 // Elementwise helpers on small matrices (row-major).
 // B[i][j] = A[i][j] * dl[i] * dr[j]  (dl / dr may be NULL = ones)

@@ -341,9 +341,9 @@ class Solver {
   // symmetric eigen-decomposition of the n x n device matrix A (ld lda),
   // ascending w to the host, V to dV (n x n, ld n)
   bdg_status eigh_dev(int n, const double* A, int lda, double* dw, double* dV, std::vector<double>& w,
-                      double floor_rel = 0.0) {
+                      double floor_rel = 0.0, bool from_identity = false) {
     if (n > SMALL_MAX) return fail(plan_, BDG_ERR_UNSUPPORTED, "projected problem larger than supported");
-    bdg_status st = cuda(eigh(n, A, lda, dw, dV, dws_, 3, s_, floor_rel), "eigh");
+    bdg_status st = cuda(eigh(n, A, lda, dw, dV, dws_, 3, s_, floor_rel, from_identity), "eigh");
     if (st) return st;
     if ((st = download(dw, w, n))) return st;
     if (dbg_eigh_) check_eigh(n, A, lda, dV, w);
@@ -518,7 +518,9 @@ class Solver {
       ldt = n;
     }
     std::vector<double> lam;
-    bdg_status st = eigh_dev(n, Kt, ldt, dvec_, Q, lam, 1e-11);   // lam <= 1e-10 lam_max is cut
+    // stage 2 (scale == false) re-solves matrices that are diagonal up to
+    // the rounding of stage 1: the refinement starts from the identity
+    bdg_status st = eigh_dev(n, Kt, ldt, dvec_, Q, lam, 1e-11, !scale);   // lam <= 1e-10 lam_max is cut
     if (st) return st;
     const double lmax = lam[n - 1];
     if (!(lmax > 0)) return fail(plan_, BDG_ERR_BREAKDOWN, "projected H_+ is not positive");
@@ -542,7 +544,7 @@ class Solver {
     if ((st = cuda(dsym_small(r, C, r, s_), "sym"))) return st;
     double* Z = dmat_[MAT_E];
     std::vector<double> w2;
-    if ((st = eigh_dev(r, C, r, dvec_, Z, w2))) return st;
+    if ((st = eigh_dev(r, C, r, dvec_, Z, w2, 0.0, !scale))) return st;
     const double cut = zero_tol2_;
     int j0 = 0;
     while (j0 < r && !(w2[j0] > cut)) ++j0;
