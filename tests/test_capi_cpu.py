@@ -66,3 +66,37 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.bdg_apply(None, 0, 0, None, None, 1, None) == bdg.ERR_INVALID
     assert lib.bdg_plan_destroy(None) == bdg.OK
     assert b"plan is NULL" in lib.bdg_last_error(None)
+
+
+def test_null_and_range_checks_of_every_entry_point(lib):
+    """Argument checks that run before any device work, for the entry points
+    added after the product: solve, bi-orthonormalisation, ground state and
+    the allocation-free chemical potentials."""
+    import ctypes
+    from paper_2506_08308_gb300 import bdg
+    import numpy as np
+    nconv = ctypes.c_int(0)
+    rank = ctypes.c_int(0)
+    om = np.zeros(4)
+    assert lib.bdg_solve(None, 4, 8, None, bdg._dptr(om), None, None, ctypes.byref(nconv), None) == bdg.ERR_INVALID
+    assert lib.bdg_biortho(None, bdg.C128, None, None, 4, None, None, 0, ctypes.byref(rank), None) == bdg.ERR_INVALID
+    assert lib.bdg_chemical_potentials_noalloc(None, bdg._dptr(np.zeros(3)), None) == bdg.ERR_INVALID
+    prm = bdg.make_params((16,), (-4.0,), (4.0,), 1.0, 0.0)
+    V, phi0 = np.zeros(16), np.ones(48)
+    out, mu, res = np.zeros(48), np.zeros(3), np.zeros(1)
+    it = ctypes.c_int(0)
+    # magnetisation outside (-1, 1) and a non-positive tolerance are refused on the host
+    assert lib.bdg_ground_state(ctypes.byref(prm), 1.5, bdg._dptr(V), bdg._dptr(phi0), 1e-12, 10, bdg._dptr(out),
+                                bdg._dptr(mu), bdg._dptr(res), ctypes.byref(it), None) == bdg.ERR_INVALID
+    assert lib.bdg_ground_state(ctypes.byref(prm), 0.0, bdg._dptr(V), bdg._dptr(phi0), 0.0, 10, bdg._dptr(out),
+                                bdg._dptr(mu), bdg._dptr(res), ctypes.byref(it), None) == bdg.ERR_INVALID
+    assert lib.bdg_ground_state(None, 0.0, None, None, 1e-12, 10, None, None, None, None, None) == bdg.ERR_INVALID
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """The package has no CPU path: without libbdg.so every call raises."""
+    from paper_2506_08308_gb300 import bdg
+    monkeypatch.setattr(bdg, "LIBPATH", str(tmp_path / "libbdg.so"))
+    monkeypatch.setattr(bdg, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        bdg.load()
