@@ -151,6 +151,19 @@ bdg_status bdg_biortho(bdg_plan_t plan, int dtype, void* F, void* G, int ncol, c
 bdg_status bdg_solve(bdg_plan_t plan, int k, int m, const void* X0, double* omega, void* UV,
                      double* resid, int* nconv, void* stream);
 
+/*
+ * bdg_solve_batched -- the k[i] smallest positive excitations of count
+ * independent problems (the batched workload: many parameter sets and grids,
+ * eqs. lrep-d and constrain for each), solved back to back on one stream.
+ * Each entry behaves as bdg_solve(plans[i], k[i], m[i], NULL, omega[i],
+ * UV ? UV[i] : NULL, resid ? resid[i] : NULL, &nconv[i], stream) with the
+ * plan's seeded start block.  Every plan is attempted; the first failing
+ * status is returned (bdg_last_error(NULL) names the plan), and nconv[i] is
+ * filled for all entries.
+ */
+bdg_status bdg_solve_batched(bdg_plan_t* plans, int count, const int* k, const int* m, double** omega,
+                             void** UV, double** resid, int* nconv, void* stream);
+
 /* Counters of the last bdg_solve on this plan. */
 typedef struct {
   int iterations;          /* outer iterations (both phases) */

@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "BDG_OK", 1: "BDG_ERR_INVALID", 2: "BDG_ERR_NOMEM", 3: "BDG_E
 
 # every symbol include/bdg.h declares
 EXPORTS = ("bdg_plan_create", "bdg_plan_destroy", "bdg_plan_mu", "bdg_apply", "bdg_biortho",
-           "bdg_solve", "bdg_get_solve_stats", "bdg_ground_state", "bdg_chemical_potentials_noalloc",
+           "bdg_solve", "bdg_solve_batched", "bdg_get_solve_stats", "bdg_ground_state",
+           "bdg_chemical_potentials_noalloc",
            "bdg_last_error")
 
 
@@ -72,6 +73,9 @@ def load() -> ctypes.CDLL:
     lib.bdg_apply.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp]
     lib.bdg_biortho.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, vp, vp, ctypes.c_int, ip, vp]
     lib.bdg_solve.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, dp, vp, dp, ip, vp]
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    dpp = ctypes.POINTER(ctypes.POINTER(ctypes.c_double))
+    lib.bdg_solve_batched.argtypes = [pp, ctypes.c_int, ip, ip, dpp, pp, dpp, ip, vp]
     lib.bdg_get_solve_stats.argtypes = [vp, ctypes.POINTER(SolveStats)]
     lib.bdg_ground_state.argtypes = [ctypes.POINTER(Params), ctypes.c_double, dp, dp, ctypes.c_double,
                                      ctypes.c_int, dp, dp, dp, ip, vp]
@@ -224,6 +228,30 @@ class Plan:
         s = SolveStats()
         _check(self.lib, self.lib.bdg_get_solve_stats(self.handle, ctypes.byref(s)), self.handle)
         return {f: getattr(s, f) for f, _ in SolveStats._fields_}
+
+
+def solve_batched(plans, ks, ms, want_vectors: bool = True, stream=None, allow_not_converged: bool = False):
+    """bdg_solve_batched over independent plans: a list of (omega, UV or None,
+    resid, nconv) per plan."""
+    import torch
+    lib = load()
+    n = len(plans)
+    dptr_t = ctypes.POINTER(ctypes.c_double)
+    oms = [np.zeros(k) for k in ks]
+    res = [np.zeros(k) for k in ks]
+    uvs = [torch.empty((k, 6, p.npts), dtype=torch.complex128, device="cuda") if want_vectors else None
+           for k, p in zip(ks, plans)]
+    h = (ctypes.c_void_p * n)(*[p.handle for p in plans])
+    karr = (ctypes.c_int * n)(*ks)
+    marr = (ctypes.c_int * n)(*ms)
+    oarr = (dptr_t * n)(*[_dptr(o) for o in oms])
+    rarr = (dptr_t * n)(*[_dptr(r) for r in res])
+    uarr = (ctypes.c_void_p * n)(*[(u.data_ptr() if u is not None else None) for u in uvs])
+    nconv = (ctypes.c_int * n)()
+    st = lib.bdg_solve_batched(h, n, karr, marr, oarr, uarr, rarr, nconv, _stream_handle(stream))
+    if not (allow_not_converged and st == ERR_NOT_CONVERGED):
+        _check(lib, st)
+    return [(oms[i], uvs[i], res[i], nconv[i]) for i in range(n)]
 
 
 def ground_state(prm: Params, M: float, V: np.ndarray, phi0: np.ndarray, tol: float = 1e-12,

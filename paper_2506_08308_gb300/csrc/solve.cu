@@ -1081,3 +1081,25 @@ bdg_status bdg_solve(bdg_plan_t plan, int k, int m, const void* X0, double* omeg
 }
 
 }  // extern "C"
+
+// Independent problems back to back on one stream (the batched workload of
+// many parameter sets and grids): each plan is solved as by bdg_solve; the
+// first failing status is returned after every plan has been attempted, and
+// nconv[i] is filled for every plan.
+extern "C" bdg_status bdg_solve_batched(bdg_plan_t* plans, int count, const int* k, const int* m,
+                                        double** omega, void** UV, double** resid, int* nconv, void* stream) {
+  if (count < 0 || (count > 0 && (!plans || !k || !m || !omega || !nconv)))
+    return fail(nullptr, BDG_ERR_INVALID, "plans, k, m, omega and nconv must hold count entries");
+  for (int i = 0; i < count; ++i)
+    if (!plans[i] || !omega[i]) return fail(nullptr, BDG_ERR_INVALID, "plan or omega entry is NULL");
+  bdg_status first = BDG_OK;
+  for (int i = 0; i < count; ++i) {
+    const bdg_status st = bdg_solve(plans[i], k[i], m[i], nullptr, omega[i], UV ? UV[i] : nullptr,
+                                    resid ? resid[i] : nullptr, &nconv[i], stream);
+    if (st != BDG_OK && first == BDG_OK) {
+      first = st;
+      set_thread_error("plan " + std::to_string(i) + ": " + plans[i]->err);
+    }
+  }
+  return first;
+}

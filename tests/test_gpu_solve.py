@@ -106,3 +106,27 @@ def test_solve_rejects_bad_sizes():
         plan.solve(8, 200)
     assert e.value.status == bdg.ERR_UNSUPPORTED
     plan.close()
+
+
+def test_solve_batched_matches_single_solves():
+    """bdg_solve_batched over three independent problems of different grids
+    (1-D, 2-D, 3-D): each entry equals its own bdg_solve and the dense FP64
+    eigenvalues."""
+    need_torch_cuda()
+    from paper_2506_08308_gb300 import bdg
+    cases = [W1, W2, W3]
+    plans, dense = [], []
+    for w in cases:
+        V, phi, mu, op = oracle_problem(w)
+        plans.append(make_plan(w, V, phi, prec=bdg.FP64, tol=1e-10, maxit=600, seed=w.block_seed + 11))
+        dense.append(_dense(op, w.k))
+    out = bdg.solve_batched(plans, [w.k for w in cases], [w.m for w in cases])
+    for w, plan, (om, UV, resid, nconv), dn in zip(cases, plans, out, dense):
+        assert nconv == w.k
+        np.testing.assert_allclose(om, dn[0][:w.k], rtol=1e-10, atol=0)
+        om1, _, _, nconv1 = plan.solve(w.k, w.m, want_vectors=False)
+        assert nconv1 == w.k
+        np.testing.assert_allclose(om, om1, rtol=1e-10, atol=0)
+        assert np.all(resid <= 1e-10)
+    for p in plans:
+        p.close()
