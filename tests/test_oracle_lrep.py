@@ -189,3 +189,26 @@ def test_table1_case1_fm(ground):
         pe, pu = gold["e_omega"][key], gold["e_uv"][key]
         assert abs(eom - pe) < 0.01 * pe, (key, eom, pe)
         assert abs(euv - pu) < 0.3 * pu, (key, euv, pu)
+
+
+def test_linear_zeeman_is_absorbed_at_fixed_magnetization(ground):
+    """Reading of the Zeeman term: with the magnetization M fixed, the linear
+    term -p S_z only shifts mu_1 - mu_-1 (a Lagrange multiplier), so the ground
+    state and the whole BdG spectrum do not depend on p.  Placing p anywhere
+    but on the diagonal of A (e.g. in B) would break this."""
+    import dataclasses
+    w0 = synth.Workload("zq1d", (64,), (-8.0,), (8.0,), (1.0,), 10.0, -1.0, 0.0, 0.1, M=0.2, gs_seed=7)
+    w1 = dataclasses.replace(w0, p=0.05)
+    spectra, phis, mus = [], [], []
+    for w in (w0, w1):
+        op, phi = _op(ground, w)
+        om, _, _ = lrep.dense_solve_fg(op, 8)
+        spectra.append(om)
+        phis.append(phi.reshape(3, -1))
+        mus.append(op.mu)
+    np.testing.assert_allclose(spectra[1], spectra[0], rtol=1e-9, atol=1e-9)
+    err = min(np.abs(phis[1] - phis[0]).max(), np.abs(phis[1] + phis[0]).max())
+    assert err < 1e-8
+    # the multipliers carry the shift: mu_1 - mu_-1 changes by 2 p
+    d0, d1 = mus[0][0] - mus[0][2], mus[1][0] - mus[1][2]
+    assert abs((d1 - d0) - 2 * 0.05) < 1e-8 or abs((d1 - d0) + 2 * 0.05) < 1e-8
