@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--skip-launch-count", action="store_true", help="leave out the profiler pass")
     ap.add_argument("--apply-only", action="store_true",
                     help="time only the block product of the workload (profiling aid; no JSON line)")
+    ap.add_argument("--profile-solve", type=int, default=0, metavar="ITERS",
+                    help="run ITERS solver iterations of the workload and exit (profiling aid; no JSON line)")
     return ap.parse_args()
 
 
@@ -283,6 +285,27 @@ def run_apply_only(args):
     plan.close()
 
 
+def run_profile_solve(args):
+    """A few FP64 solver iterations of the workload on an operator built from
+    the normalised seeded start spinor (no ground state, so that a profiler
+    sees few launches before the solver's); prints the time per iteration."""
+    import torch
+    from paper_2506_08308_gb300 import bdg
+    w = W
+    phi = synth.initial_spinor(w)
+    phi = phi / np.sqrt(np.prod(w.h) * np.sum(phi ** 2))
+    plan = bdg.Plan(bdg.params_from(w, mu=(5.7, 5.7, 5.7), prec=bdg.FP64, tol=TOL, maxit=args.profile_solve),
+                    synth.potential(w), phi.reshape(-1))
+    X0 = torch.from_numpy(synth.random_block(w, w.m, complex_=True)).cuda()
+    t0 = time.perf_counter()
+    plan.solve(w.k, w.m, X0=X0, want_vectors=False, allow_not_converged=True)
+    torch.cuda.synchronize()
+    st = plan.stats()
+    print(f"profile-solve {w.name}: {st['iterations']} iterations, "
+          f"{(time.perf_counter() - t0) / max(st['iterations'], 1) * 1e3:.1f} ms/iteration", flush=True)
+    plan.close()
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -459,6 +482,8 @@ def main():
         run_reference(args)
     elif args.apply_only:
         run_apply_only(args)
+    elif args.profile_solve > 0:
+        run_profile_solve(args)
     else:
         run_ours(args)
 
