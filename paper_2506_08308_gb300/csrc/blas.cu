@@ -109,15 +109,15 @@ __device__ __forceinline__ void df_fma(float& sh, float& sl, float ah, float al,
 // tiles on or above the diagonal are formed.
 template <int MP, int MQ>
 __global__ void __launch_bounds__(256) k_gram_partial_df(PairBlock<double> A, PairBlock<double> B,
-                                                         double* __restrict__ part, int upper) {
+                                                         double* __restrict__ part, int upper, long long crows) {
   constexpr int TP = 16 * MP, TQ = 16 * MQ;
   if (upper && blockIdx.y < blockIdx.x) return;
   __shared__ float sAh[GK][TP + 4], sAl[GK][TP + 4];
   __shared__ float sBh[GK][TQ + 4], sBl[GK][TQ + 4];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int i0 = blockIdx.x * TP, j0 = blockIdx.y * TQ;
-  const long long r_begin = (long long)blockIdx.z * GROWS;
-  const long long r_end = min(A.n, r_begin + GROWS);
+  const long long r_begin = (long long)blockIdx.z * crows;
+  const long long r_end = min(A.n, r_begin + crows);
   const int P2 = 2 * A.cols, Q2 = 2 * B.cols;
   float ah_[MP][MQ], al_[MP][MQ];
 #pragma unroll
@@ -359,9 +359,22 @@ cudaError_t gram_pairs(const PairBlock<R>& A, const PairBlock<R>& B, double* G_d
     int mp = tile_mult(P2), mq = tile_mult(Q2);
     const bool up = upper && P2 == Q2;
     if (up) mp = mq = std::max(mp, mq);
-    dim3 g8((P2 + 16 * mp - 1) / (16 * mp), (Q2 + 16 * mq - 1) / (16 * mq), (unsigned)nchunks);
+    // narrow blocks have few output tiles: shorter row chunks (more CTAs, up
+    // to about four per SM) as far as the workspace holds their partial sums
+    const long long tiles = (long long)((P2 + 16 * mp - 1) / (16 * mp)) * ((Q2 + 16 * mq - 1) / (16 * mq));
+    long long crows = GROWS, nch = nchunks;
+    const long long want = (4 * 152 + tiles - 1) / tiles;
+    if (want > nch) {
+      const long long cap = (long long)(ws_bytes / (sizeof(double) * (size_t)P2 * Q2));
+      long long target = std::min(want, cap);
+      if (target > nch) {
+        crows = ((A.n + target - 1) / target + GK - 1) / GK * GK;
+        nch = (A.n + crows - 1) / crows;
+      }
+    }
+    dim3 g8((P2 + 16 * mp - 1) / (16 * mp), (Q2 + 16 * mq - 1) / (16 * mq), (unsigned)nch);
 #define BDG_GDF(MP_, MQ_) \
-  if (mp == MP_ && mq == MQ_) k_gram_partial_df<MP_, MQ_><<<g8, 256, 0, s>>>(A8, B8, (double*)ws, up ? 1 : 0);
+  if (mp == MP_ && mq == MQ_) k_gram_partial_df<MP_, MQ_><<<g8, 256, 0, s>>>(A8, B8, (double*)ws, up ? 1 : 0, crows);
     BDG_GDF(1, 1) BDG_GDF(1, 2) BDG_GDF(1, 3) BDG_GDF(1, 4)
     BDG_GDF(2, 1) BDG_GDF(2, 2) BDG_GDF(2, 3) BDG_GDF(2, 4)
     BDG_GDF(3, 1) BDG_GDF(3, 2) BDG_GDF(3, 3) BDG_GDF(3, 4)
@@ -370,7 +383,7 @@ cudaError_t gram_pairs(const PairBlock<R>& A, const PairBlock<R>& B, double* G_d
     cudaError_t e8 = cudaGetLastError();
     if (e8 != cudaSuccess) return e8;
     const int nout8 = P2 * Q2;
-    k_gram_reduce_upper<<<(nout8 + 255) / 256, 256, 0, s>>>((const double*)ws, (int)nchunks, P2, Q2,
+    k_gram_reduce_upper<<<(nout8 + 255) / 256, 256, 0, s>>>((const double*)ws, (int)nch, P2, Q2,
                                                             up ? 16 * mp : (1 << 30), G_dev);
     return cudaGetLastError();
   }
