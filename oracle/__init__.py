@@ -23,6 +23,8 @@ Modules, each citing the passages it follows:
                   eq. constrainfg.
   kohn            the analytical eigenpairs of Theorem "Analytical eigenpairs"
                   (eq. eig-pair) and the error metrics of Section 4.1.
+  perturbed       the perturbed densities of single modes (Section 4.2,
+                  eq. waveAssump with one mode).
 
 Parity status: every function is pinned by a `-m "not gpu"` test against
 closed forms, invariants or library routines, except the iterates of the
