@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--skip-launch-count", action="store_true", help="leave out the profiler pass")
     ap.add_argument("--apply-only", action="store_true",
                     help="time only the block product of the workload (profiling aid; no JSON line)")
+    ap.add_argument("--density-only", action="store_true",
+                    help="time only the perturbed densities of the workload's modes (one JSON line per precision)")
     ap.add_argument("--profile-solve", type=int, default=0, metavar="ITERS",
                     help="run ITERS solver iterations of the workload and exit (profiling aid; no JSON line)")
     return ap.parse_args()
@@ -285,6 +287,65 @@ def run_apply_only(args):
     plan.close()
 
 
+# FP64 arithmetic of GB300 (nominal dense rate; an FMA counts two flops)
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def run_density_only(args):
+    """bdg_perturbed_density on the workload's k modes (random amplitudes of
+    the solver's output shape), one snapshot t = 10.6 with eps = 0.1, the
+    setting of the paper's density figures.  L2 is flushed before every timed
+    launch (a 256 MB write), each launch is timed alone with CUDA events, and
+    one JSON line per precision gives the kernel's roofline: the FP32 kernel
+    against the measured HBM copy rate, the FP64 kernel against the FP64
+    pipe (14 flops per point, component and mode at one time: four sums,
+    two products of two terms, one add and a sum of two squares)."""
+    import torch
+    from paper_2506_08308_gb300 import bdg
+    w = W
+    phi = synth.initial_spinor(w)
+    phi = phi / np.sqrt(np.prod(w.h) * np.sum(phi ** 2))
+    plan = bdg.Plan(bdg.params_from(w, mu=(1.0, 1.0, 1.0)), synth.potential(w), phi.reshape(-1))
+    UV = torch.from_numpy(synth.random_block(w, w.k, seed=2024) * 0.05).cuda()
+    om = np.linspace(1.0, 3.0, w.k)
+    times = [10.6]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    peaks, how = measured_peaks()
+    stream = torch.cuda.current_stream()
+    for dt, esz in ((torch.complex64, 8), (torch.complex128, 16)):
+        x = UV.to(dt)
+        out = plan.perturbed_density(x, om, times, 0.1)
+        for _ in range(max(args.warmup, 1)):
+            plan.perturbed_density(x, om, times, 0.1, out=out)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(max(args.steps, 1)):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.perturbed_density(x, om, times, 0.1, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = float(np.median(ms)) / 1e3
+        rsz = esz // 2
+        nbytes = w.k * w.npts * (6 * esz + 3 * len(times) * rsz) + w.npts * 4 * rsz
+        flops = 14 * 3 * w.k * w.npts * len(times)
+        line = {"kernel": "k_perturbed_density", "dtype": "f32" if esz == 8 else "f64",
+                "workload": w.name, "modes": w.k, "times": len(times), "us_per_launch": t * 1e6,
+                "algorithmic_bytes": nbytes, "l2": "flushed before each launch"}
+        if esz == 8:
+            line["roofline"] = {"bound": "hbm", "achieved": nbytes / t / 1e9, "peak": peaks["hbm_gbs"],
+                                "unit": "GB/s", "frac": nbytes / t / 1e9 / peaks["hbm_gbs"],
+                                "peak_source": how}
+        else:
+            line["roofline"] = {"bound": "alu", "achieved": flops / t / 1e12, "peak": FP64_NOMINAL_TFLOPS,
+                                "unit": "TFLOP/s", "frac": flops / t / 1e12 / FP64_NOMINAL_TFLOPS,
+                                "peak_source": "nominal FP64", "hbm_gbs": nbytes / t / 1e9}
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def run_profile_solve(args):
     """A few FP64 solver iterations of the workload on an operator built from
     the normalised seeded start spinor (no ground state, so that a profiler
@@ -482,6 +543,8 @@ def main():
         run_reference(args)
     elif args.apply_only:
         run_apply_only(args)
+    elif args.density_only:
+        run_density_only(args)
     elif args.profile_solve > 0:
         run_profile_solve(args)
     else:

@@ -212,6 +212,33 @@ bdg_status bdg_ground_state(const bdg_params* p, double M, const double* V, cons
  */
 bdg_status bdg_chemical_potentials_noalloc(bdg_plan_t plan, double* mu, void* stream);
 
+/*
+ * bdg_perturbed_density -- perturbed densities of excitation modes
+ * (Section 4.2, the "2D Case" example; the ansatz eq. waveAssump with one
+ * mode l kept):
+ *   n_j^l(x, t) = | phi_j(x) + eps ( u_j^l(x) e^{-i omega_l t}
+ *                                   + conj(v_j^l(x)) e^{i omega_l t} ) |^2,
+ * j = 1, 0, -1, with phi the plan's ground state, for nmode modes and nt times.
+ *   dtype  BDG_C128: FP64 arithmetic, double output;  BDG_C64: FP32
+ *          arithmetic (phi rounded to FP32), float output.  The phases
+ *          (eps cos omega t, eps sin omega t) are formed in FP64 on the host
+ *          (and rounded to FP32 for BDG_C64).
+ *   UV     [in, device] [nmode][6][N_p] complex of dtype in the UV form
+ *          (u_1, u_0, u_-1, v_1, v_0, v_-1), e.g. as bdg_solve writes it.
+ *   omega  [in, host] double[nmode];  times [in, host] double[nt].
+ *   eps    the amplitude of the perturbation (finite).
+ *   out    [out, device] [nmode][nt][3][N_p] real of dtype's precision;
+ *          must not overlap UV.
+ * nmode == 0 or nt == 0 is a no-op; nmode <= 65535.  Non-finite omega,
+ * times or eps return BDG_ERR_INVALID.  With nmode * nt <= 128 the phase
+ * table is passed with the launch and the call does not wait for the
+ * stream.  Longer tables are copied from pageable host memory into plan
+ * scratch: that copy first waits for the stream, and consecutive calls on
+ * one plan must then be stream-ordered.
+ */
+bdg_status bdg_perturbed_density(bdg_plan_t plan, int dtype, const void* UV, int nmode, const double* omega,
+                                 const double* times, int nt, double eps, void* out, void* stream);
+
 /* bdg_last_error -- message of the last failing call on plan (NULL: of the
  * last failing plan-less call on this thread).  Never NULL. */
 const char* bdg_last_error(bdg_plan_t plan);

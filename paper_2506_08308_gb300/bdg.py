@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "BDG_OK", 1: "BDG_ERR_INVALID", 2: "BDG_ERR_NOMEM", 3: "BDG_E
 # every symbol include/bdg.h declares
 EXPORTS = ("bdg_plan_create", "bdg_plan_destroy", "bdg_plan_mu", "bdg_apply", "bdg_biortho",
            "bdg_solve", "bdg_solve_batched", "bdg_get_solve_stats", "bdg_ground_state",
-           "bdg_chemical_potentials_noalloc",
+           "bdg_chemical_potentials_noalloc", "bdg_perturbed_density",
            "bdg_last_error")
 
 
@@ -80,6 +80,8 @@ def load() -> ctypes.CDLL:
     lib.bdg_ground_state.argtypes = [ctypes.POINTER(Params), ctypes.c_double, dp, dp, ctypes.c_double,
                                      ctypes.c_int, dp, dp, dp, ip, vp]
     lib.bdg_chemical_potentials_noalloc.argtypes = [vp, dp, vp]
+    lib.bdg_perturbed_density.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, dp, dp, ctypes.c_int,
+                                          ctypes.c_double, vp, vp]
     lib.bdg_last_error.argtypes = [vp]
     lib.bdg_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -195,6 +197,31 @@ class Plan:
             out = torch.empty_like(x)
         st = self.lib.bdg_apply(self.handle, int(mode), dt, _ptr(x), _ptr(out), int(x.shape[0]),
                                 _stream_handle(stream))
+        _check(self.lib, st, self.handle)
+        return out
+
+    def perturbed_density(self, UV, omega, times, eps: float, out=None, stream=None):
+        """bdg_perturbed_density: n[l, t, j, x] = |phi_j + eps (u_j^l e^{-i w_l t} +
+        conj(v_j^l) e^{i w_l t})|^2 for a CUDA tensor UV of shape (nmode, 6, N_p)
+        (complex128 -> float64 result, complex64 -> float32), shape
+        (nmode, nt, 3, N_p)."""
+        import torch
+        if not UV.is_cuda or UV.dim() != 3 or UV.shape[1] != 6 or UV.shape[2] != self.npts:
+            raise ValueError("UV must be a CUDA tensor of shape (nmode, 6, N_p)")
+        dt = {torch.complex128: C128, torch.complex64: C64}.get(UV.dtype)
+        if dt is None:
+            raise ValueError("UV must be complex64 or complex128")
+        UV = UV.contiguous()
+        nmode = int(UV.shape[0])
+        om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64).reshape(-1))
+        ts = np.ascontiguousarray(np.asarray(times, dtype=np.float64).reshape(-1))
+        if om.size != nmode:
+            raise ValueError("omega needs one value per mode")
+        if out is None:
+            out = torch.empty((nmode, ts.size, 3, self.npts), device=UV.device,
+                              dtype=torch.float64 if dt == C128 else torch.float32)
+        st = self.lib.bdg_perturbed_density(self.handle, dt, _ptr(UV), nmode, _dptr(om), _dptr(ts), int(ts.size),
+                                            float(eps), _ptr(out), _stream_handle(stream))
         _check(self.lib, st, self.handle)
         return out
 

@@ -98,7 +98,7 @@ struct bdg_plan_s {
   double* zg64 = nullptr;
   float* zf32 = nullptr;
   float* zg32 = nullptr;
-  bdg::Buffer scratch[8];
+  bdg::Buffer scratch[9];   // indexed by ScratchSlot
   std::string err;
   bdg_solve_stats stats;
   void* last_stream = nullptr;

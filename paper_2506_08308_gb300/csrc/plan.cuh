@@ -15,7 +15,10 @@ enum ScratchSlot {
   SLOT_SOLVER2 = 5,
   SLOT_SOLVER3 = 6,
   SLOT_AUX = 7,
+  SLOT_PHASE = 8,   // phase tables of the perturbed densities
+  SLOT_COUNT = 9,
 };
+static_assert(sizeof(bdg_plan_s::scratch) / sizeof(Buffer) == SLOT_COUNT, "one scratch buffer per slot");
 
 // y = M x with the plan's chemical potentials, or mu_override if non-NULL.
 bdg_status apply_internal(bdg_plan_t plan, int mode, int dtype, const void* x, void* y, int nvec,

@@ -70,8 +70,8 @@ def test_invalid_arguments_rejected_on_host(lib):
 
 def test_null_and_range_checks_of_every_entry_point(lib):
     """Argument checks that run before any device work, for the entry points
-    added after the product: solve, bi-orthonormalisation, ground state and
-    the allocation-free chemical potentials."""
+    added after the product: solve, bi-orthonormalisation, ground state, the
+    allocation-free chemical potentials and the perturbed densities."""
     import ctypes
     from paper_2506_08308_gb300 import bdg
     import numpy as np
@@ -81,6 +81,9 @@ def test_null_and_range_checks_of_every_entry_point(lib):
     assert lib.bdg_solve(None, 4, 8, None, bdg._dptr(om), None, None, ctypes.byref(nconv), None) == bdg.ERR_INVALID
     assert lib.bdg_biortho(None, bdg.C128, None, None, 4, None, None, 0, ctypes.byref(rank), None) == bdg.ERR_INVALID
     assert lib.bdg_chemical_potentials_noalloc(None, bdg._dptr(np.zeros(3)), None) == bdg.ERR_INVALID
+    t1 = np.zeros(1)
+    assert lib.bdg_perturbed_density(None, bdg.C128, None, 1, bdg._dptr(t1), bdg._dptr(t1), 1, 0.1, None,
+                                     None) == bdg.ERR_INVALID
     prm = bdg.make_params((16,), (-4.0,), (4.0,), 1.0, 0.0)
     V, phi0 = np.zeros(16), np.ones(48)
     out, mu, res = np.zeros(48), np.zeros(3), np.zeros(1)
