@@ -801,6 +801,17 @@ class Solver {
       const int na = (int)act.size();
       const int nap = (na + 1) / 2;
       if (log_) fprintf(stderr, "[bdg]   active %d of %d, P %d\n", na, mm, haveP ? 1 : 0);
+      if (na == 0) {
+        // Every Ritz pair meets tol, so there is no search direction.  This
+        // happens when the block is wide enough that its extra pairs converge
+        // with the wanted ones.  The pending check re-runs the Ritz step on
+        // the block alone, with exact images.
+        if (!refresh_next)
+          return fail(plan_, BDG_ERR_BREAKDOWN, "all Ritz pairs converged but fewer than k were found");
+        nxb = 0;
+        nu = mm;
+        continue;
+      }
       if (dbg_ && haveP) fprintf(stderr, "[bdg]   dbg P images before gather %.3e\n", dbg_img(Pb_, HPb_, mmp));
       if (dbg_ && haveP) {
         // gather check on a copy: G = P Sel must equal the selected columns
