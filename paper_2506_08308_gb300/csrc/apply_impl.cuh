@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(192) k_row(const typename CT<R>::T* __restrict
                                              Coupling<R> cp, R kscale, int mode) {
   typedef typename CT<R>::T T;
   typedef Line<N, T, WarpSync> L;
-  constexpr int N1 = L::N1, N2 = L::N2, RR = 32 / N1, NL = 6 * RR;
+  constexpr int N1 = L::N1, N2 = L::N2, RR = 32 / N1, NL = 6 * RR, NT = 192;
+  static_assert(NL * N == NT * N2, "the staging loop gives every thread N2 elements");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tw = reinterpret_cast<T*>(smem_raw);
   T* xbuf = tw + N;         // [NL][N]
@@ -101,28 +102,50 @@ __global__ void __launch_bounds__(192) k_row(const typename CT<R>::T* __restrict
   const int tid = threadIdx.x;
   const long long u0 = (long long)blockIdx.x * RR;
 
-  for (int i = tid; i < N; i += blockDim.x) tw[i] = twg[i];
-  // stage x (line l = c*RR + r)
-  for (int idx = tid; idx < NL * N; idx += blockDim.x) {
-    const int l = idx / N, i = idx - l * N;
-    const int c = l / RR, r = l - c * RR;
+  for (int i = tid; i < N; i += NT) tw[i] = twg[i];
+  // stage x (line l = c*RR + r): NL*N = NT*N2 elements, N2 per thread, in
+  // batches of KB loads issued before their stores so that the latencies
+  // overlap; the per-point table of the coupling loop below is fetched first
+  constexpr int NP = (RR * N + NT - 1) / NT;   // coupling points per thread
+  typename CT<R>::Q q[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int pidx = tid + k * NT;
+    const int r = pidx / N, i = pidx - r * N;
     const long long u = u0 + r;
-    T v = mk((R)0, (R)0);
-    if (u < nunits) {
-      const long long vec = u / rows_per_vec, row = u - vec * rows_per_vec;
-      v = x[(vec * 6 + c) * npts + row * N + i];
+    if (pidx < RR * N && u < nunits) q[k] = phiv[(u % rows_per_vec) * N + i];
+  }
+  constexpr int KB = N2 >= 8 ? 8 : N2;
+  static_assert(N2 % KB == 0, "whole batches");
+#pragma unroll
+  for (int k0 = 0; k0 < N2; k0 += KB) {
+    T v[KB];
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      const int idx = tid + (k0 + k) * NT;
+      const int l = idx / N, i = idx - l * N;
+      const int c = l / RR, r = l - c * RR;
+      const long long u = u0 + r;
+      v[k] = mk((R)0, (R)0);
+      if (u < nunits) {
+        const long long vec = u / rows_per_vec, row = u - vec * rows_per_vec;
+        v[k] = x[(vec * 6 + c) * npts + row * N + i];
+      }
     }
-    xbuf[idx] = v;
+#pragma unroll
+    for (int k = 0; k < KB; ++k) xbuf[tid + (k0 + k) * NT] = v[k];
   }
   __syncthreads();
   // pointwise coupling
-  for (int pidx = tid; pidx < RR * N; pidx += blockDim.x) {
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int pidx = tid + k * NT;
+    if (pidx >= RR * N) break;
     const int r = pidx / N, i = pidx - r * N;
     const long long u = u0 + r;
     if (u >= nunits) continue;
-    const long long row = u % rows_per_vec;
     Sym3<R> A, B;
-    coupling_blocks<R>(phiv[row * N + i], cp, A, B);
+    coupling_blocks<R>(q[k], cp, A, B);
     const T x0 = xbuf[(0 * RR + r) * N + i], x1 = xbuf[(1 * RR + r) * N + i],
             x2 = xbuf[(2 * RR + r) * N + i], x3 = xbuf[(3 * RR + r) * N + i],
             x4 = xbuf[(4 * RR + r) * N + i], x5 = xbuf[(5 * RR + r) * N + i];
@@ -189,7 +212,7 @@ __global__ void __launch_bounds__(192) k_row(const typename CT<R>::T* __restrict
 // W adjacent lines per CTA, thread (w, j): w = tid % W, j = tid / W.
 // ---------------------------------------------------------------------------
 template <int N, typename R, int W>
-__global__ void __launch_bounds__(W * Split<N>::N1) k_axis(const typename CT<R>::T* __restrict__ x,
+__global__ void __launch_bounds__(W * Split<N>::N1, (sizeof(R) == 4 && N <= 256) ? 512 / (W * Split<N>::N1) : 1) k_axis(const typename CT<R>::T* __restrict__ x,
                                                           typename CT<R>::T* __restrict__ y,
                                                           long long npts, long long st,
                                                           long long tiles_per_comp,
@@ -230,11 +253,14 @@ __global__ void __launch_bounds__(W * Split<N>::N1) k_axis(const typename CT<R>:
   const int c = (int)(vc % 6);
   const R sg = (mode == BDG_UV && c >= 3) ? (R)-1 : (R)1;
   T* yl = y + base;
+  // all N2 reads of y first: with a runtime stride the compiler cannot tell
+  // the elements apart, and a read-add-write per element would wait out one
+  // memory latency per element
+  T yv[N2];
 #pragma unroll
-  for (int n2 = 0; n2 < N2; ++n2) {
-    const long long o = (long long)(j + N1 * n2) * st;
-    yl[o] = cfma(a[n2], sg, yl[o]);
-  }
+  for (int n2 = 0; n2 < N2; ++n2) yv[n2] = yl[(long long)(j + N1 * n2) * st];
+#pragma unroll
+  for (int n2 = 0; n2 < N2; ++n2) yl[(long long)(j + N1 * n2) * st] = cfma(a[n2], sg, yv[n2]);
 }
 
 // ---------------------------------------------------------------------------
