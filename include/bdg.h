@@ -133,7 +133,8 @@ bdg_status bdg_biortho(bdg_plan_t plan, int dtype, void* F, void* G, int ncol, c
  * Bogoliubov amplitudes (Sections 3.1-3.2; solver details are this library's
  * own, see the design notes).
  *   k       number of wanted pairs, 1 <= k <= m.
- *   m       block size (k <= m <= 256).
+ *   m       block size, k <= m <= 58 (the projected problems of three
+ *           blocks must fit the on-chip eigensolver; BDG_ERR_UNSUPPORTED beyond).
  *   X0      optional device start block, [m][6][N_p] C128 in the FG form (only
  *           the real parts are used); NULL => seeded internal block.
  *   omega   [out, host] double[k], ascending.

@@ -1049,7 +1049,8 @@ bdg_status bdg_solve(bdg_plan_t plan, int k, int m, const void* X0, double* omeg
   if (!omega || !nconv) return fail(plan, BDG_ERR_INVALID, "omega and nconv must be host pointers");
   if (k < 1 || m < k || 3 * ((m + 1) / 2) * 2 > SMALL_MAX + 16)
     return fail(plan, k < 1 || m < k ? BDG_ERR_INVALID : BDG_ERR_UNSUPPORTED,
-                "need 1 <= k <= m and 3 m <= " + std::to_string(SMALL_MAX));
+                "need 1 <= k <= m <= 58 (three blocks of m rounded up to even within " +
+                    std::to_string(SMALL_MAX + 16) + " projected columns)");
   cudaStream_t s = (cudaStream_t)stream;
   plan->last_stream = stream;
   memset(&plan->stats, 0, sizeof(plan->stats));

@@ -105,6 +105,10 @@ def test_solve_rejects_bad_sizes():
     with pytest.raises(bdg.BdgError) as e:
         plan.solve(8, 200)
     assert e.value.status == bdg.ERR_UNSUPPORTED
+    # the largest block the header allows is 58; 59 is refused before any work
+    with pytest.raises(bdg.BdgError) as e:
+        plan.solve(8, 59)
+    assert e.value.status == bdg.ERR_UNSUPPORTED and "58" in str(e.value)
     plan.close()
 
 
