@@ -13,7 +13,15 @@ baseline, SM clocks sampled during the timed region, and kernel launches.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank solves its own independent instance (weak scaling,
-no collective on the data path).
+no collective on the data path).  Each solve is capped at SOLVE_MAXIT
+iterations and counts only the pairs that reached the tolerance.
+
+Single-kernel modes (one JSON line per precision, no solve):
+  --apply-only [--apply-config 2|3|5]  the block product on the 256^2,
+                                       128^3 or 256^3 workload
+  --density-only                       the perturbed densities of the
+                                       256^2 workload's 32 modes
+  --profile-solve ITERS                a few solver iterations, for profilers
 """
 import argparse
 import hashlib
