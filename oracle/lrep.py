@@ -108,20 +108,34 @@ def biortho(F, G, Fl=None, Gl=None, rtol=1e-12):
     return F @ (X[:, :r] * sc), G @ (Yh[:r].conj().T * sc), r
 
 
-def small_lrep(Kp, Km, zero_tol=1e-8):
+def small_lrep(Kp, Km, zero_tol=1e-8, rank_tol=1e-10):
     """Eigenpairs of the projected pencil: K_- q = omega p, K_+ p = omega q
     with K_+ = L L^T, eigh(L^T K_- L) = Z diag(omega^2) Z^T, p = L^-T z,
     q = L z / omega, scaled so p_i^T q_i = 1.  Returns (omega, Pc, Qc) for the
-    omega > zero_tol, ascending."""
+    omega > zero_tol, ascending.
+
+    K_+ is only semidefinite when the basis holds a direction of null(H_+)
+    (the spin rotations of a ground state with full spin symmetry leave such
+    directions outside Z_f).  The factor is therefore rank-revealing, as in
+    reading P17: with D = diag(K_+)^-1/2 and D K_+ D = Q diag(lam) Q^T,
+    L = D^-1 Q_r lam_r^1/2 over the lam > rank_tol max(lam), and L^-T is
+    the pseudo-inverse D Q_r lam_r^-1/2 on that subspace."""
     Kp = 0.5 * (Kp + Kp.T)
     Km = 0.5 * (Km + Km.T)
-    L = np.linalg.cholesky(Kp)
+    dd = np.sqrt(np.maximum(np.diag(Kp), 0.0))
+    live = dd > 1e-150 * max(dd.max(), 1e-300)      # zero columns stay out
+    d = np.where(live, 1.0 / np.where(live, dd, 1.0), 0.0)
+    lam, Q = np.linalg.eigh((Kp * d[:, None]) * d[None, :])
+    keep = lam > rank_tol * lam.max()
+    lam, Q = lam[keep], Q[:, keep]
+    L = (Q * np.sqrt(lam)) * dd[:, None]
+    Lit = (Q / np.sqrt(lam)) * d[:, None]
     C = L.T @ Km @ L
     w2, Z = np.linalg.eigh(0.5 * (C + C.T))
     pos = w2 > zero_tol ** 2
     w2, Z = w2[pos], Z[:, pos]
     om = np.sqrt(w2)
-    Pc = sla.solve_triangular(L.T, Z, lower=False)
+    Pc = Lit @ Z
     Qc = (L @ Z) / om
     s = np.sqrt(om)          # p^T q = z^T z / omega = 1 / omega before scaling
     return om, Pc * s, Qc * s
@@ -188,7 +202,7 @@ def _vecs(X, P):
 
 
 def solve_iterative(op, k, m, X0, Zf, Zg, tol=1e-10, maxit=1000, sigma=None,
-                    rtol=1e-10, verbose=False):
+                    rtol=1e-5, refresh_every=20, verbose=False):
     """Block structure-preserving subspace iteration (reading P8; after the
     LOBP4dCG family the paper cites for BOSP).  Real arithmetic.
 
@@ -200,7 +214,9 @@ def solve_iterative(op, k, m, X0, Zf, Zg, tol=1e-10, maxit=1000, sigma=None,
     of g along Z_f or of f along Z_g; after each Rayleigh-Ritz step they are
     set by the residual-minimizing closed form
     g <- g + Z_f Z_f^T (H_+ f - w g) / w  (and symmetrically for f).  Preconditioner
-    T_sigma = IDFT (1/2|mu|^2 + sigma)^-1 DFT (reading P10).
+    T_sigma = IDFT (1/2|mu|^2 + sigma)^-1 DFT (reading P10).  The
+    bi-orthonormalization keeps singular values >= rtol sigma_max (reading
+    P16), and the images H X are recomputed every refresh_every iterations.
 
     X0: (m, 6, P) real FG start.  Returns (omega[k], F[k,3,P], G[k,3,P],
     resid[k], iterations)."""
@@ -238,6 +254,13 @@ def solve_iterative(op, k, m, X0, Zf, Zg, tol=1e-10, maxit=1000, sigma=None,
         mm = min(m, om_all.size)
         om, Pc, Qc = om_all[:mm], Pc[:, :mm], Qc[:, :mm]
         F, G, HF, HG = U @ Pc, V @ Qc, HU @ Pc, HV @ Qc
+        if it % refresh_every == 0:
+            # the images carried by linear combination drift from H X by
+            # rounding; recompute them (and drop the previous update, whose
+            # images drifted the same way)
+            HF, HG = hp(F), hm(G)
+            nF = 0
+            Pf = Pg = HPf = HPg = None
         if nF > 0:
             Pf, HPf = U[:, nF:] @ Pc[nF:], HU[:, nF:] @ Pc[nF:]
             Pg, HPg = V[:, nF:] @ Qc[nF:], HV[:, nF:] @ Qc[nF:]

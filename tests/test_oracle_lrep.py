@@ -169,6 +169,25 @@ def test_iterative_solver_matches_dense(ground):
     assert r.max() < 1e-9
 
 
+def test_iterative_solver_table1_fm_case(ground):
+    """The oracle's subspace iteration on the Table 1 FM case at h0/2
+    (beta_n = 885.4, beta_s = -4.1: a ground state with full spin symmetry,
+    whose rotation about y gives a direction of null(H_+) outside Z_f, so the
+    projected H_+ is only semidefinite): the 20 smallest pairs to residual
+    2e-10, the dense eigenvalues to 1e-9, and the Kohn mode's e_omega to
+    1 % of the printed 9.570e-5."""
+    w = synth.Workload("t1_64", (64,), (-16.0,), (16.0,), (1.0,), 885.4, -4.1, k=20, m=40, gs_seed=17,
+                       block_seed=18)
+    op, phi = _op(ground, w)
+    Zf, Zg = lrep.deflation_bases(op, phi)
+    X0 = synth.random_block(w, w.m, complex_=False)
+    om, F, G, res, it = lrep.solve_iterative(op, w.k, w.m, X0, Zf, Zg, tol=1e-10, maxit=800)
+    assert res.max() <= 2e-10, res
+    om_d, _, _ = lrep.dense_solve_fg(op, w.k)
+    assert np.allclose(om, om_d, rtol=1e-9, atol=0)
+    assert abs(abs(om[17] - 1.0) - 9.570e-05) < 0.01 * 9.570e-05, om[17]
+
+
 def test_table1_case1_fm(ground):
     """Table 1 (Example "Accuracy", Case I, 1D FM, beta_n = 885.4,
     beta_s = -4.1, L = 16, gamma_x = 1; M not stated, read as 0): the
