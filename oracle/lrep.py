@@ -145,7 +145,8 @@ def small_lrep(Kp, Km, zero_tol=1e-8, rank_tol=1e-10):
 # deflation
 # --------------------------------------------------------------------------
 def deflation_bases(op, phi, par_tol=1e-12, null_tol=1e-8):
-    """Orthonormal Z_f (n x 1..2) and Z_g (n x 0..1), n = 3P (reading P7)."""
+    """Orthonormal Z_f (n x 1..3) and Z_g (n x 0..1), n = 3P (reading P7):
+    Phi and S_z Phi always, S_x Phi and -i S_y Phi when numerically null."""
     phi = np.asarray(phi, dtype=np.float64).reshape(3, -1)
     P = phi.shape[1]
     z1 = phi.ravel() / np.linalg.norm(phi)
@@ -155,6 +156,23 @@ def deflation_bases(op, phi, par_tol=1e-12, null_tol=1e-8):
     if np.linalg.norm(r) > par_tol * max(np.linalg.norm(sz), 1e-300) and np.linalg.norm(sz) > par_tol:
         r = r - z1 * (z1 @ r)
         cols.append(r / np.linalg.norm(r))
+    # S_x Phi = (1/sqrt2) (phi_0, phi_1 + phi_-1, phi_0): the rotation about x
+    # is a symmetry too when the state is symmetric enough (antiferromagnetic
+    # or polar states at p = q = 0); kept when its part outside
+    # span{Phi, S_z Phi} is numerically in null(H_-)
+    sx = np.concatenate([phi[1], phi[0] + phi[2], phi[1]]) / np.sqrt(2.0)
+    nsx = np.linalg.norm(sx)
+    if nsx > par_tol * np.linalg.norm(phi):
+        r = sx.copy()
+        for _ in range(2):
+            for c in cols:
+                r = r - c * (c @ r)
+        nr = np.linalg.norm(r)
+        if nr > 1e-6 * nsx:
+            r = r / nr
+            hr = op.hminus(r.reshape(1, 3, P)).ravel()
+            if np.linalg.norm(hr) < null_tol:
+                cols.append(r)
     Zf = np.stack(cols, axis=1)
     # -i S_y Phi = (1/sqrt2) (-phi_0, phi_1 - phi_-1, phi_0)
     y = np.concatenate([-phi[1], phi[0] - phi[2], phi[1]]) / np.sqrt(2.0)

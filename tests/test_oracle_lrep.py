@@ -188,6 +188,33 @@ def test_iterative_solver_table1_fm_case(ground):
     assert abs(abs(om[17] - 1.0) - 9.570e-05) < 0.01 * 9.570e-05, om[17]
 
 
+def test_deflation_and_iterative_solver_afm_case(ground):
+    """Table 1's AFM instance at h0/2 (beta_n = 240.8, beta_s = 7.5, p = q = 0):
+    the ground state (phi_1, 0, phi_-1) is also symmetric under the rotation
+    about x, so S_x Phi lies in null(H_-) (checked here against the product
+    directly) and joins Z_f; without it the subspace iteration locks onto a
+    spurious near-zero pair.  With it the iteration meets the dense
+    eigenvalues to 1e-9 at residual 2e-10.  The ferromagnetic state keeps
+    Z_f = span{Phi, S_z Phi} (its S_x Phi is parallel to Phi)."""
+    w = synth.Workload("t1a_64", (64,), (-16.0,), (16.0,), (1.0,), 240.8, 7.5, k=12, m=24, gs_seed=17,
+                       block_seed=18)
+    op, phi = _op(ground, w)
+    p = phi.reshape(3, -1)
+    sx = np.concatenate([p[1], p[0] + p[2], p[1]]) / np.sqrt(2.0)
+    assert np.linalg.norm(op.hminus(sx.reshape(1, 3, -1))) < 1e-10 * np.linalg.norm(sx)
+    Zf, Zg = lrep.deflation_bases(op, phi)
+    assert Zf.shape[1] == 3 and np.allclose(Zf.T @ Zf, np.eye(3), atol=1e-12)
+    X0 = synth.random_block(w, w.m, complex_=False)
+    om, F, G, res, it = lrep.solve_iterative(op, w.k, w.m, X0, Zf, Zg, tol=1e-10, maxit=800)
+    assert res.max() <= 2e-10, res
+    om_d, _, _ = lrep.dense_solve_fg(op, w.k)
+    assert np.allclose(om, om_d, rtol=1e-9, atol=0)
+    wf = synth.Workload("t1_64", (64,), (-16.0,), (16.0,), (1.0,), 885.4, -4.1, gs_seed=17)
+    opf, phif = _op(ground, wf)
+    Zff, Zgf = lrep.deflation_bases(opf, phif)
+    assert Zff.shape[1] == 2 and Zgf.shape[1] == 1
+
+
 def test_table1_case1_fm(ground):
     """Table 1 (Example "Accuracy", Case I, 1D FM, beta_n = 885.4,
     beta_s = -4.1, L = 16, gamma_x = 1; M not stated, read as 0): the
