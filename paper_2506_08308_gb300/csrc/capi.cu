@@ -156,8 +156,8 @@ static bdg_status dot_cols(bdg_plan_t plan, const void* a, const void* b, long l
 }
 
 // Build the real vectors used at set-up from (phi_1, phi_0, phi_-1, V):
-// kind 0: [0,0,0, phi] (FG vector), 1: Phi, 2: S_z Phi, 3: -i S_y Phi
-// (f-part 3 x N_p complex with zero imaginary parts).
+// kind 0: [0,0,0, phi] (FG vector), 1: Phi, 2: S_z Phi, 3: -i S_y Phi,
+// 4: S_x Phi (f-part 3 x N_p complex with zero imaginary parts).
 __global__ void k_build(const dquad* __restrict__ pv, long long np, int kind, double2* __restrict__ out) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < np;
        i += (long long)gridDim.x * blockDim.x) {
@@ -165,7 +165,8 @@ __global__ void k_build(const dquad* __restrict__ pv, long long np, int kind, do
     double c0, c1, c2;
     if (kind == 0 || kind == 1) { c0 = v.x; c1 = v.y; c2 = v.z; }
     else if (kind == 2) { c0 = v.x; c1 = 0.0; c2 = -v.z; }
-    else { const double h = 0.70710678118654752440; c0 = -h * v.y; c1 = h * (v.x - v.z); c2 = h * v.y; }
+    else if (kind == 3) { const double h = 0.70710678118654752440; c0 = -h * v.y; c1 = h * (v.x - v.z); c2 = h * v.y; }
+    else { const double h = 0.70710678118654752440; c0 = h * v.y; c1 = h * (v.x + v.z); c2 = h * v.y; }
     if (kind == 0) {
       out[i] = make_double2(0.0, 0.0);
       out[np + i] = make_double2(0.0, 0.0);
@@ -225,16 +226,37 @@ static bdg_status compute_mu(bdg_plan_t plan, cudaStream_t s, double* mu) {
   return BDG_OK;
 }
 
+// z -= w (w . z) for the unit column w, as pair coefficients (imaginary parts zero)
+static bdg_status subtract_projection(bdg_plan_t plan, const double2* w, double2* z, long long n3,
+                                      cudaStream_t s) {
+  double d;
+  bdg_status st = dot_cols<double>(plan, w, z, n3, &d, s);
+  if (st) return st;
+  double hC[4] = {-d, 0.0, 0.0, -d};
+  st = ensure(plan, SLOT_SMALL, 64 * sizeof(double));
+  if (st) return st;
+  double* C = (double*)plan->scratch[SLOT_SMALL].ptr;
+  BDG_CUDA_TRY(plan, cudaMemcpyAsync(C, hC, sizeof(hC), cudaMemcpyHostToDevice, s));
+  PairBlock<double> A{w, n3, n3, 1};
+  BDG_CUDA_TRY(plan, update_pairs<double>(A, C, 2, 1.0, z, n3, 1, s));
+  BDG_CUDA_TRY(plan, cudaStreamSynchronize(s));
+  return BDG_OK;
+}
+
 // Deflation bases (Section 2.3; Theorems on null(H_-) and null(H_+)):
 // Z_f = orthonormal span{Phi, S_z Phi} (in null(H_-) for a ground state),
-// S_z Phi dropped when (numerically) parallel to Phi or zero;
+// S_z Phi dropped when (numerically) parallel to Phi or zero, plus the part
+// of S_x Phi outside that span when it is numerically in null(H_-) (states
+// symmetric under the rotation about x: antiferromagnetic or polar at
+// p = q = 0; every f of a pair with omega != 0 is H_- g / omega, so any
+// null(H_-) vector may be deflated);
 // Z_g = {-i S_y Phi / |.|} when |H_+ z| / |z| < 1e-8 (in null(H_+)).
 static bdg_status build_deflation(bdg_plan_t plan, cudaStream_t s) {
   const long long np = plan->grid.npts, n3 = 3 * np;
   std::vector<double2*> cols;
   double2* zf = nullptr;
   double2* zg = nullptr;
-  BDG_CUDA_TRY(plan, cudaMalloc(&zf, sizeof(double2) * 2 * n3));
+  BDG_CUDA_TRY(plan, cudaMalloc(&zf, sizeof(double2) * 3 * n3));
   BDG_CUDA_TRY(plan, cudaMalloc(&zg, sizeof(double2) * n3));
   plan->zf64 = (double*)zf;
   plan->zg64 = (double*)zg;
@@ -276,6 +298,42 @@ static bdg_status build_deflation(bdg_plan_t plan, cudaStream_t s) {
     BDG_CUDA_TRY(plan, scale_pairs<double>(zf + n3, n3, n3, 1, nullptr, 1.0 / std::sqrt(nz), s));
     nzf = 2;
   }
+  {
+    // S_x Phi in the next column: orthogonalized twice against Z_f, kept
+    // when a direction of relative size > 1e-6 is left and |H_- z| < 1e-8
+    double2* zc = zf + nzf * n3;
+    k_build<<<blocks_for(np), 256, 0, s>>>(plan->phiv64, np, 4, zc);
+    BDG_CUDA_TRY(plan, cudaGetLastError());
+    double nsx;
+    st = dot_cols<double>(plan, zc, zc, n3, &nsx, s);
+    if (st) return st;
+    if (nsx > 1e-24 * nn1) {
+      for (int pass = 0; pass < 2; ++pass)
+        for (int j = 0; j < nzf; ++j)
+          if ((st = subtract_projection(plan, zf + j * n3, zc, n3, s))) return st;
+      double nr;
+      st = dot_cols<double>(plan, zc, zc, n3, &nr, s);
+      if (st) return st;
+      if (nr > 1e-12 * nsx) {
+        BDG_CUDA_TRY(plan, scale_pairs<double>(zc, n3, n3, 1, nullptr, 1.0 / std::sqrt(nr), s));
+        st = ensure(plan, SLOT_VEC_A, sizeof(double2) * 6 * np);
+        if (st) return st;
+        st = ensure(plan, SLOT_VEC_B, sizeof(double2) * 6 * np);
+        if (st) return st;
+        double2* x = (double2*)plan->scratch[SLOT_VEC_A].ptr;
+        double2* y = (double2*)plan->scratch[SLOT_VEC_B].ptr;
+        // H_- z is the g-part of the FG product of (0, z)
+        BDG_CUDA_TRY(plan, cudaMemsetAsync(x, 0, sizeof(double2) * 6 * np, s));
+        BDG_CUDA_TRY(plan, cudaMemcpyAsync(x + n3, zc, sizeof(double2) * n3, cudaMemcpyDeviceToDevice, s));
+        st = apply_internal(plan, BDG_FG, BDG_C128, x, y, 1, s, nullptr);
+        if (st) return st;
+        double nh;
+        st = dot_cols<double>(plan, y + n3, y + n3, n3, &nh, s);
+        if (st) return st;
+        if (std::sqrt(nh) < 1e-8) nzf++;
+      }
+    }
+  }
   plan->nzf = nzf;
   // Z_g candidate: H_+ z via the FG product of (z, 0)
   double ny;
@@ -302,9 +360,9 @@ static bdg_status build_deflation(bdg_plan_t plan, cudaStream_t s) {
     }
   }
   // FP32 copies
-  BDG_CUDA_TRY(plan, cudaMalloc(&plan->zf32, sizeof(float2) * 2 * n3));
+  BDG_CUDA_TRY(plan, cudaMalloc(&plan->zf32, sizeof(float2) * 3 * n3));
   BDG_CUDA_TRY(plan, cudaMalloc(&plan->zg32, sizeof(float2) * n3));
-  BDG_CUDA_TRY(plan, (convert_pairs<double, float>(zf, n3, (float2*)plan->zf32, n3, n3, 2, s)));
+  BDG_CUDA_TRY(plan, (convert_pairs<double, float>(zf, n3, (float2*)plan->zf32, n3, n3, 3, s)));
   BDG_CUDA_TRY(plan, (convert_pairs<double, float>(zg, n3, (float2*)plan->zg32, n3, n3, 1, s)));
   BDG_CUDA_TRY(plan, cudaStreamSynchronize(s));
   return BDG_OK;

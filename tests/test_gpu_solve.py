@@ -4,7 +4,8 @@ amplitudes per degenerate cluster to 1e-8 (projector metric of Section 4.1),
 residuals <= 1e-10 in FP64, and the normalization / bi-orthogonality
 h^d (u_i.u_j - v_i.v_j) = delta_ij (eq. constrain, Theorem
 "Biorthogonality"); FP64 and mixed precision, 1-D, 2-D and 3-D, odd and even
-block sizes, a start block passed in and the internal seeded one."""
+block sizes, a start block passed in and the internal seeded one, and an
+antiferromagnetic state whose deflation space holds S_x Phi."""
 import numpy as np
 import pytest
 
@@ -22,6 +23,10 @@ W2 = synth.Workload("s2d_16", (16, 16), (-6.0, -6.0), (6.0, 6.0), (1.0, 1.4), 12
 W3 = synth.Workload("s3d_8", (8, 8, 8), (-4.0,) * 3, (4.0,) * 3, (1.0, 1.2, 1.5), 8.0, -0.5, 0.02, 0.2, k=6,
                     m=10, gs_seed=31, block_seed=32)
 WC1 = synth.CONFIG1
+# Table 1's antiferromagnetic instance at h0/2 (p = q = 0): its ground state
+# (phi_1, 0, phi_-1) puts S_x Phi in null(H_-), a third column of Z_f
+WAFM = synth.Workload("t1a_64", (64,), (-16.0,), (16.0,), (1.0,), 240.8, 7.5, 0.0, 0.0, k=8, m=16,
+                      gs_seed=17, block_seed=18)
 
 
 def _dense(op, k):
@@ -58,7 +63,7 @@ def _check(w, op, om, UV, resid, k, dense):
     assert r.max() < 1e-9, r
 
 
-@pytest.mark.parametrize("w", [W1, W1Q, W2, W3], ids=lambda w: w.name)
+@pytest.mark.parametrize("w", [W1, W1Q, W2, W3, WAFM], ids=lambda w: w.name)
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_solve_matches_dense(w, prec):
     torch = need_torch_cuda()
