@@ -237,6 +237,27 @@ def test_table1_case1_fm(ground):
         assert abs(euv - pu) < 0.3 * pu, (key, euv, pu)
 
 
+def test_table1_case1_afm_eigenvector_errors(ground):
+    """Table 1's Anti-FM row (Case I, 1D, beta_n = 240.8, beta_s = 7.5,
+    L = 16, gamma_x = 1; M read as 0): the Kohn-mode eigenvector error e_uv
+    at h0/2 and h0/4 reproduces the printed values to 5 %.  Its eigenvalue
+    error e_omega is not pinned: this restatement gives 2.0e-4 and 1.4e-9
+    against the printed 1.83e-4 and 3.3e-10.  The FM row matches in both
+    metrics."""
+    with open(os.path.join(HERE, "golden", "table1_case1_afm.json")) as fh:
+        gold = json.load(fh)
+    for n, key in ((64, "h0/2"), (128, "h0/4")):
+        w = synth.Workload(f"t1a_{n}", (n,), (-16.0,), (16.0,), (1.0,), 240.8, 7.5, gs_seed=17)
+        op, phi = _op(ground, w)
+        om, F, G = lrep.dense_solve_fg(op, 12)
+        i = int(np.argmin(np.abs(om - 1.0)))
+        (gam, f, g), = kohn.kohn_modes(w, phi)
+        euv = kohn.e_uv((F[i] + G[i]).ravel(), (F[i] - G[i]).ravel(),
+                        (f + g).ravel()[:, None], (f - g).ravel()[:, None])
+        pu = gold["e_uv"][key]
+        assert abs(euv - pu) < 0.05 * pu, (key, euv, pu)
+
+
 def test_linear_zeeman_is_absorbed_at_fixed_magnetization(ground):
     """Reading of the Zeeman term: with the magnetization M fixed, the linear
     term -p S_z only shifts mu_1 - mu_-1 (a Lagrange multiplier), so the ground
