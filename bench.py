@@ -17,8 +17,8 @@ no collective on the data path).  Each solve is capped at SOLVE_MAXIT
 iterations and counts only the pairs that reached the tolerance.
 
 Single-kernel modes (one JSON line per precision, no solve):
-  --apply-only [--apply-config 2|3|5]  the block product on the 256^2,
-                                       128^3 or 256^3 workload
+  --apply-only [--apply-workload W]    the block product on the 2d_n256,
+                                       3d_n128 or 3d_n256 workload
   --density-only                       the perturbed densities of the
                                        256^2 workload's 32 modes
   --profile-solve ITERS                a few solver iterations, for profilers
@@ -42,7 +42,7 @@ import synth  # noqa: E402
 
 METRIC = "BdG-apply HBM GB/s; converged eigenpairs/s at resid 1e-10, mixed vs FP64"
 UNIT = "eigenpairs/s"
-W = synth.CONFIG2
+W = synth.W2D_N256
 TOL = 1e-10
 # Iterations the block solver needs on this workload (the device mixed solve
 # from the seeded start block); the CPU timings are extrapolated to it.
@@ -64,8 +64,8 @@ def parse():
     ap.add_argument("--skip-launch-count", action="store_true", help="leave out the profiler pass")
     ap.add_argument("--apply-only", action="store_true",
                     help="time only the block product (one JSON line per precision)")
-    ap.add_argument("--apply-config", type=int, default=2, choices=[2, 3, 5],
-                    help="workload of --apply-only: 2 (256^2, m 48), 3 (128^3, m 48), 5 (256^3, m 32 / 16 in FP64)")
+    ap.add_argument("--apply-workload", default="2d_n256", choices=["2d_n256", "3d_n128", "3d_n256"],
+                    help="workload of --apply-only: 256^2 (m 48), 128^3 (m 48) or 256^3 (m 32, 16 in FP64)")
     ap.add_argument("--density-only", action="store_true",
                     help="time only the perturbed densities of the workload's modes (one JSON line per precision)")
     ap.add_argument("--profile-solve", type=int, default=0, metavar="ITERS",
@@ -279,7 +279,7 @@ def run_apply_only(args):
     out, plus the per-point table (16 B or 32 B) once per call."""
     import torch
     from paper_2506_08308_gb300 import bdg
-    w = synth.CONFIGS[args.apply_config]
+    w = synth.WORKLOADS[args.apply_workload]
     phi = synth.initial_spinor(w)
     phi = phi / np.sqrt(np.prod(w.h) * np.sum(phi ** 2))
     plan = bdg.Plan(bdg.params_from(w, mu=(1.0, 1.0, 1.0)), synth.potential(w), phi.reshape(-1))

@@ -55,16 +55,18 @@ class Workload:
         return dataclasses.replace(self, n=tuple(int(v) for v in n))
 
 
-# The five workloads (1-D FP64; 2-D FP64 vs mixed; 3-D mixed; batched 2-D; large 3-D).
-CONFIG1 = Workload("1d_n256", (256,), (-16.0,), (16.0,), (1.0,), 10.0, -1.0, 0.0, 0.0,
+# The benchmark workloads, named by dimension and points per axis: the 1-D
+# FP64 case, the 2-D FP64-versus-mixed case, the 3-D mixed case and the large
+# 3-D case (the batched 2-D workload is drawn by batched_workloads below).
+W1D_N256 = Workload("1d_n256", (256,), (-16.0,), (16.0,), (1.0,), 10.0, -1.0, 0.0, 0.0,
                    k=16, m=24, gs_seed=101, block_seed=1001)
-CONFIG2 = Workload("2d_n256", (256, 256), (-12.0, -12.0), (12.0, 12.0), (1.0, 1.0),
+W2D_N256 = Workload("2d_n256", (256, 256), (-12.0, -12.0), (12.0, 12.0), (1.0, 1.0),
                    100.0, -2.0, 0.0, 0.1, k=32, m=48, gs_seed=102, block_seed=1002)
-CONFIG3 = Workload("3d_n128", (128, 128, 128), (-8.0,) * 3, (8.0,) * 3, (1.0, 1.5, 2.0),
+W3D_N128 = Workload("3d_n128", (128, 128, 128), (-8.0,) * 3, (8.0,) * 3, (1.0, 1.5, 2.0),
                    200.0, -4.0, 0.05, 0.2, k=32, m=48, gs_seed=103, block_seed=1003)
-CONFIG5 = Workload("3d_n256", (256, 256, 256), (-10.0,) * 3, (10.0,) * 3, (1.0, 1.0, 1.0),
+W3D_N256 = Workload("3d_n256", (256, 256, 256), (-10.0,) * 3, (10.0,) * 3, (1.0, 1.0, 1.0),
                    400.0, -8.0, 0.0, 0.1, k=24, m=32, gs_seed=105, block_seed=1005)
-CONFIGS = {1: CONFIG1, 2: CONFIG2, 3: CONFIG3, 5: CONFIG5}
+WORKLOADS = {w.name: w for w in (W1D_N256, W2D_N256, W3D_N128, W3D_N256)}
 
 
 def batched_workloads(count: int = 64, seed: int = 4) -> list:

@@ -20,7 +20,7 @@ r = dist.get_rank()
 bench.rank_barrier(dist)
 m = bench.reduce_max(dist, 10.0 + r, "cpu")
 seeds = [None, None]
-dist.all_gather_object(seeds, bench.instance_seed(synth.CONFIG2, r))
+dist.all_gather_object(seeds, bench.instance_seed(synth.W2D_N256, r))
 print("RESULT", r, m, seeds[0] != seeds[1], flush=True)
 dist.destroy_process_group()
 """

@@ -56,7 +56,7 @@ def test_apply_full_2d_block_sampled():
     torch = need_torch_cuda()
     from paper_2506_08308_gb300 import bdg
     from oracle import apply as ap
-    w = synth.CONFIG2
+    w = synth.W2D_N256
     V = synth.potential(w)
     rng = np.random.default_rng(3)
     # any real spinor is a valid operator input; a Gaussian keeps it smooth

@@ -122,7 +122,7 @@ def test_full_workload_sampled(dtype):
     benchmark's density line times): 4096 sampled points per mode against
     the oracle evaluated point by point."""
     torch = need_torch_cuda()
-    w = synth.CONFIG2
+    w = synth.W2D_N256
     phi = _phi(w)
     plan = _plan(w, phi)
     UV = synth.random_block(w, w.k, seed=2024) * 0.05

@@ -22,7 +22,7 @@ W2 = synth.Workload("s2d_16", (16, 16), (-6.0, -6.0), (6.0, 6.0), (1.0, 1.4), 12
                     gs_seed=8, block_seed=3)
 W3 = synth.Workload("s3d_8", (8, 8, 8), (-4.0,) * 3, (4.0,) * 3, (1.0, 1.2, 1.5), 8.0, -0.5, 0.02, 0.2, k=6,
                     m=10, gs_seed=31, block_seed=32)
-WC1 = synth.CONFIG1
+WC1 = synth.W1D_N256
 # Table 1's antiferromagnetic instance at h0/2 (p = q = 0): its ground state
 # (phi_1, 0, phi_-1) puts S_x Phi in null(H_-), a third column of Z_f
 WAFM = synth.Workload("t1a_64", (64,), (-16.0,), (16.0,), (1.0,), 240.8, 7.5, 0.0, 0.0, k=8, m=16,
@@ -81,7 +81,7 @@ def test_solve_matches_dense(w, prec):
     plan.close()
 
 
-def test_solve_config1_full_size():
+def test_solve_1d_n256_full_size():
     """The 1-D workload as specified: N = 256, k = 16, m = 24, FP64, seeded
     internal start block."""
     torch = need_torch_cuda()
