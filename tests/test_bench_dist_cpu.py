@@ -60,3 +60,29 @@ def test_reference_arm_prints_on_rank0_only(capsys, monkeypatch):
         gpus, steps, warmup, cpu_iters = 2, 1, 0, 1
     bench.run_reference(A())
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_json_contract(capsys, monkeypatch):
+    """Rank 0 of the CPU reference arm prints exactly one JSON line with the
+    keys the benchmark contract names, on the same metric, unit and workload
+    as the GPU arm; one oracle iteration keeps it short."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+
+    class A:
+        gpus, steps, warmup, cpu_iters = 1, 1, 0, 1
+    bench.run_reference(A())
+    lines = [x for x in capsys.readouterr().out.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["config"]["workload"] == bench.W.name and d["value"] > 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
