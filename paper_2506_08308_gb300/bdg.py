@@ -110,6 +110,15 @@ def _dptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def _check_out(out, shape, dtype, device):
+    """A caller-supplied output tensor must match exactly: the library writes
+    prod(shape) elements of dtype through its pointer and cannot see its size."""
+    if (tuple(out.shape) != tuple(shape) or out.dtype != dtype or out.device != device
+            or not out.is_contiguous()):
+        raise ValueError(f"out must be a contiguous {dtype} tensor of shape {tuple(shape)} on {device}, "
+                         f"got {out.dtype} {tuple(out.shape)} on {out.device}")
+
+
 def make_params(n: Sequence[int], lo: Sequence[float], hi: Sequence[float], beta_n: float,
                 beta_s: float, p: float = 0.0, q: float = 0.0, mu=None, prec: int = FP64,
                 tol: float = 1e-10, maxit: int = 500, seed: int = 1) -> Params:
@@ -195,6 +204,7 @@ class Plan:
         x = x.contiguous()
         if out is None:
             out = torch.empty_like(x)
+        _check_out(out, x.shape, x.dtype, x.device)
         st = self.lib.bdg_apply(self.handle, int(mode), dt, _ptr(x), _ptr(out), int(x.shape[0]),
                                 _stream_handle(stream))
         _check(self.lib, st, self.handle)
@@ -217,9 +227,10 @@ class Plan:
         ts = np.ascontiguousarray(np.asarray(times, dtype=np.float64).reshape(-1))
         if om.size != nmode:
             raise ValueError("omega needs one value per mode")
+        rdt = torch.float64 if dt == C128 else torch.float32
         if out is None:
-            out = torch.empty((nmode, ts.size, 3, self.npts), device=UV.device,
-                              dtype=torch.float64 if dt == C128 else torch.float32)
+            out = torch.empty((nmode, ts.size, 3, self.npts), device=UV.device, dtype=rdt)
+        _check_out(out, (nmode, ts.size, 3, self.npts), rdt, UV.device)
         st = self.lib.bdg_perturbed_density(self.handle, dt, _ptr(UV), nmode, _dptr(om), _dptr(ts), int(ts.size),
                                             float(eps), _ptr(out), _stream_handle(stream))
         _check(self.lib, st, self.handle)

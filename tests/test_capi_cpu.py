@@ -103,3 +103,19 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(bdg, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         bdg.load()
+
+
+def test_output_tensor_checks_of_the_binding():
+    """The binding refuses a caller-supplied output tensor whose shape, dtype,
+    device or layout differ from what the library will write."""
+    torch = pytest.importorskip("torch")
+    from paper_2506_08308_gb300 import bdg
+    good = torch.empty((2, 1, 3, 8), dtype=torch.float64)
+    bdg._check_out(good, (2, 1, 3, 8), torch.float64, good.device)
+    for bad, why in ((torch.empty((2, 1, 3, 7), dtype=torch.float64), "shape"),
+                     (torch.empty((2, 1, 3, 8), dtype=torch.float32), "dtype"),
+                     (torch.empty((2, 1, 8, 3), dtype=torch.float64).transpose(2, 3), "layout")):
+        with pytest.raises(ValueError):
+            bdg._check_out(bad, (2, 1, 3, 8), torch.float64, good.device)
+    with pytest.raises(ValueError):
+        bdg._check_out(good, (2, 1, 3, 8), torch.float64, torch.device("meta"))
