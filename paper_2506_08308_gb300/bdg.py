@@ -240,8 +240,18 @@ class Plan:
         """In-place bi-orthonormalization of F, G (CUDA, (ncol, 3, N_p) complex);
         returns the rank kept."""
         import torch
-        dt = {torch.complex128: C128, torch.complex64: C64}[F.dtype]
+        dt = {torch.complex128: C128, torch.complex64: C64}.get(F.dtype)
+        if dt is None or not F.is_cuda or F.dim() != 3:
+            raise ValueError("F must be a complex64/complex128 CUDA tensor of shape (ncol, 3, N_p)")
+        shape = (int(F.shape[0]), 3, self.npts)
+        _check_out(F, shape, F.dtype, F.device)      # updated in place: exact shape, contiguous
+        _check_out(G, shape, F.dtype, F.device)
         nlock = 0 if Fl is None else int(Fl.shape[0])
+        if nlock:
+            if Gl is None:
+                raise ValueError("Fl and Gl go together")
+            _check_out(Fl, (nlock, 3, self.npts), F.dtype, F.device)
+            _check_out(Gl, (nlock, 3, self.npts), F.dtype, F.device)
         rank = ctypes.c_int(0)
         st = self.lib.bdg_biortho(self.handle, dt, _ptr(F), _ptr(G), int(F.shape[0]), _ptr(Fl),
                                   _ptr(Gl), nlock, ctypes.byref(rank), _stream_handle(stream))
@@ -256,6 +266,10 @@ class Plan:
         resid = np.zeros(k)
         nconv = ctypes.c_int(0)
         UVt = torch.empty((k, 6, self.npts), dtype=torch.complex128, device="cuda") if want_vectors else None
+        if X0 is not None:
+            if not X0.is_cuda:
+                raise ValueError("X0 must be a CUDA tensor")
+            _check_out(X0, (m, 6, self.npts), torch.complex128, X0.device)
         st = self.lib.bdg_solve(self.handle, int(k), int(m), _ptr(X0), _dptr(omega), _ptr(UVt),
                                 _dptr(resid), ctypes.byref(nconv), _stream_handle(stream))
         if not (allow_not_converged and st == ERR_NOT_CONVERGED):

@@ -119,3 +119,20 @@ def test_output_tensor_checks_of_the_binding():
             bdg._check_out(bad, (2, 1, 3, 8), torch.float64, good.device)
     with pytest.raises(ValueError):
         bdg._check_out(good, (2, 1, 3, 8), torch.float64, torch.device("meta"))
+
+
+def test_binding_checks_blocks_before_the_library():
+    """biortho and solve check the blocks they hand to the library (device,
+    dtype, exact shape, contiguity) before any call: exercised on a plan
+    object that has no library handle, so any call through would fail."""
+    torch = pytest.importorskip("torch")
+    from paper_2506_08308_gb300 import bdg
+    p = bdg.Plan.__new__(bdg.Plan)
+    p.npts, p.lib, p.handle = 8, None, None
+    cpu = torch.zeros((2, 3, 8), dtype=torch.complex128)
+    with pytest.raises(ValueError):
+        p.biortho(cpu, cpu.clone())
+    with pytest.raises(ValueError):
+        p.biortho(torch.zeros((2, 3, 8), dtype=torch.float64), cpu)
+    with pytest.raises(ValueError):
+        p.solve(2, 4, X0=torch.zeros((4, 6, 8), dtype=torch.complex128), want_vectors=False)
