@@ -133,8 +133,9 @@ bdg_status bdg_biortho(bdg_plan_t plan, int dtype, void* F, void* G, int ncol, c
  * Bogoliubov amplitudes (Sections 3.1-3.2; solver details are this library's
  * own, see the design notes).
  *   k       number of wanted pairs, 1 <= k <= m.
- *   m       block size, k <= m <= 58 (the projected problems of three
- *           blocks must fit the on-chip eigensolver; BDG_ERR_UNSUPPORTED beyond).
+ *   m       block size, k <= m <= 52 (the projected problem of three
+ *           blocks of m rounded up to even, at most 156 columns, must fit the
+ *           160-column on-chip eigensolver; BDG_ERR_UNSUPPORTED beyond).
  *   X0      optional device start block, [m][6][N_p] C128 in the FG form (only
  *           the real parts are used); NULL => seeded internal block.
  *   omega   [out, host] double[k], ascending.
@@ -208,7 +209,8 @@ bdg_status bdg_ground_state(const bdg_params* p, double M, const double* V, cons
  *     streams, threads or plans at once) race and must be serialized.
  *   - the first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) and should come before any stream capture on
- *     that device.
+ *     that device.  The address is kept until the process exits: after a
+ *     cudaDeviceReset of that device, do not call this entry point on it.
  * The call synchronizes the stream before it returns.
  */
 bdg_status bdg_chemical_potentials_noalloc(bdg_plan_t plan, double* mu, void* stream);

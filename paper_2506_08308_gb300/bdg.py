@@ -162,6 +162,10 @@ class Plan:
                                       _stream_handle(stream))
         _check(self.lib, st)
         self.handle = h
+        import torch
+        # the library records the current device at creation; outputs the
+        # binding allocates go there too
+        self.device = torch.device("cuda", torch.cuda.current_device())
 
     @classmethod
     def from_workload(cls, w, V, phi, **kw):
@@ -240,6 +244,8 @@ class Plan:
         """In-place bi-orthonormalization of F, G (CUDA, (ncol, 3, N_p) complex);
         returns the rank kept."""
         import torch
+        if (Fl is None) != (Gl is None):
+            raise ValueError("Fl and Gl go together: give both or neither")
         dt = {torch.complex128: C128, torch.complex64: C64}.get(F.dtype)
         if dt is None or not F.is_cuda or F.dim() != 3:
             raise ValueError("F must be a complex64/complex128 CUDA tensor of shape (ncol, 3, N_p)")
@@ -248,8 +254,6 @@ class Plan:
         _check_out(G, shape, F.dtype, F.device)
         nlock = 0 if Fl is None else int(Fl.shape[0])
         if nlock:
-            if Gl is None:
-                raise ValueError("Fl and Gl go together")
             _check_out(Fl, (nlock, 3, self.npts), F.dtype, F.device)
             _check_out(Gl, (nlock, 3, self.npts), F.dtype, F.device)
         rank = ctypes.c_int(0)
@@ -265,11 +269,11 @@ class Plan:
         omega = np.zeros(k)
         resid = np.zeros(k)
         nconv = ctypes.c_int(0)
-        UVt = torch.empty((k, 6, self.npts), dtype=torch.complex128, device="cuda") if want_vectors else None
         if X0 is not None:
-            if not X0.is_cuda:
-                raise ValueError("X0 must be a CUDA tensor")
+            if not X0.is_cuda or X0.device != self.device:
+                raise ValueError("X0 must be a CUDA tensor on the plan's device")
             _check_out(X0, (m, 6, self.npts), torch.complex128, X0.device)
+        UVt = torch.empty((k, 6, self.npts), dtype=torch.complex128, device=self.device) if want_vectors else None
         st = self.lib.bdg_solve(self.handle, int(k), int(m), _ptr(X0), _dptr(omega), _ptr(UVt),
                                 _dptr(resid), ctypes.byref(nconv), _stream_handle(stream))
         if not (allow_not_converged and st == ERR_NOT_CONVERGED):
@@ -291,7 +295,7 @@ def solve_batched(plans, ks, ms, want_vectors: bool = True, stream=None, allow_n
     dptr_t = ctypes.POINTER(ctypes.c_double)
     oms = [np.zeros(k) for k in ks]
     res = [np.zeros(k) for k in ks]
-    uvs = [torch.empty((k, 6, p.npts), dtype=torch.complex128, device="cuda") if want_vectors else None
+    uvs = [torch.empty((k, 6, p.npts), dtype=torch.complex128, device=p.device) if want_vectors else None
            for k, p in zip(ks, plans)]
     h = (ctypes.c_void_p * n)(*[p.handle for p in plans])
     karr = (ctypes.c_int * n)(*ks)

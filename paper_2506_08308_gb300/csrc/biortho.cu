@@ -318,6 +318,7 @@ extern "C" bdg_status bdg_biortho(bdg_plan_t plan, int dtype, void* F, void* G, 
   const size_t bytes = esz * 3 * (size_t)plan->grid.npts * ncol;
   const char *fb = (const char*)F, *gb = (const char*)G;
   if (fb < gb + bytes && gb < fb + bytes) return fail(plan, BDG_ERR_INVALID, "F and G overlap");
+  if (bdg_status sd = check_device(plan)) return sd;
   plan->last_stream = stream;
   cudaStream_t s = (cudaStream_t)stream;
   if (dtype == BDG_C128) return biortho_run<double>(plan, F, G, ncol, Fl, Gl, nlock, rank, s);

@@ -25,6 +25,16 @@ bdg_status fail(bdg_plan_t plan, bdg_status st, const std::string& msg) {
   return st;
 }
 
+bdg_status check_device(bdg_plan_t plan) {
+  int dev = -1;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(plan, BDG_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev != plan->device)
+    return fail(plan, BDG_ERR_INVALID, "the current device is " + std::to_string(dev) + " but the plan lives on device " +
+                                           std::to_string(plan->device) + "; make the plan's device current first");
+  return BDG_OK;
+}
+
 bdg_status ensure(bdg_plan_t plan, int slot, size_t bytes) {
   Buffer& b = plan->scratch[slot];
   if (b.bytes >= bytes) return BDG_OK;
@@ -498,6 +508,7 @@ bdg_status bdg_apply(bdg_plan_t plan, int mode, int dtype, const void* x, void* 
   if (dtype != BDG_C128 && dtype != BDG_C64) return fail(plan, BDG_ERR_INVALID, "dtype must be BDG_C128 or BDG_C64");
   if (nvec < 0) return fail(plan, BDG_ERR_INVALID, "nvec < 0");
   if (nvec == 0) return BDG_OK;
+  if (bdg_status sd = check_device(plan)) return sd;
   if (!x || !y) return fail(plan, BDG_ERR_INVALID, "x and y must be device pointers");
   const size_t esz = dtype == BDG_C128 ? 16 : 8;
   const size_t bytes = esz * 6 * (size_t)plan->grid.npts * (size_t)nvec;

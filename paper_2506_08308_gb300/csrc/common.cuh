@@ -107,4 +107,7 @@ struct bdg_plan_s {
 namespace bdg {
 bdg_status fail(bdg_plan_t plan, bdg_status st, const std::string& msg);
 bdg_status ensure(bdg_plan_t plan, int slot, size_t bytes);
+// BDG_OK when the calling thread's current device is the plan's device; else
+// BDG_ERR_INVALID (the plan's data would be read from another GPU).
+bdg_status check_device(bdg_plan_t plan);
 }  // namespace bdg

@@ -110,6 +110,7 @@ extern "C" bdg_status bdg_perturbed_density(bdg_plan_t plan, int dtype, const vo
   if (ib < ob + out_bytes && ob < ib + in_bytes) return fail(plan, BDG_ERR_INVALID, "UV and out overlap");
   if ((uintptr_t)UV % esz || (uintptr_t)out % rsz)
     return fail(plan, BDG_ERR_INVALID, "UV or out not aligned to its element size");
+  if (bdg_status sd = check_device(plan)) return sd;
   // phase table (eps cos w t, eps sin w t) in FP64 on the host
   std::vector<double2> tab((size_t)nmode * nt);
   for (int l = 0; l < nmode; ++l) {

@@ -22,7 +22,9 @@
 // The device address of the array is looked up once per device (with that
 // device current) by cudaGetSymbolAddress on the first call made on that
 // device; the first call on a device should therefore come before any
-// stream capture on it.
+// stream capture on it.  The address is kept for the life of the process:
+// after a cudaDeviceReset of that device it would be stale, so a process that
+// resets a device must not call this entry point on it again.
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -91,6 +93,7 @@ extern "C" bdg_status bdg_chemical_potentials_noalloc(bdg_plan_t plan, double* m
     return fail(plan, BDG_ERR_UNSUPPORTED,
                 "grid has " + std::to_string(np) + " points; the allocation-free path holds at most " +
                     std::to_string(NOALLOC_MAX_NPTS));
+  if (bdg_status sd = check_device(plan)) return sd;
   unsigned char* base = nullptr;
   bdg_status st = scratch_address(plan, &base);
   if (st) return st;

@@ -1047,10 +1047,15 @@ bdg_status bdg_solve(bdg_plan_t plan, int k, int m, const void* X0, double* omeg
                      int* nconv, void* stream) {
   if (!plan) return fail(nullptr, BDG_ERR_INVALID, "plan is NULL");
   if (!omega || !nconv) return fail(plan, BDG_ERR_INVALID, "omega and nconv must be host pointers");
-  if (k < 1 || m < k || 3 * ((m + 1) / 2) * 2 > SMALL_MAX + 16)
+  // the basis [X, P, D] holds at most 2 (mp + mp) + 2 mp = 6 mp real columns
+  // (mp = ceil(m / 2) pairs per block), and its projected problem must fit
+  // the on-chip eigensolver
+  if (k < 1 || m < k || 6 * ((m + 1) / 2) > SMALL_MAX)
     return fail(plan, k < 1 || m < k ? BDG_ERR_INVALID : BDG_ERR_UNSUPPORTED,
-                "need 1 <= k <= m <= 58 (three blocks of m rounded up to even within " +
-                    std::to_string(SMALL_MAX + 16) + " projected columns)");
+                "need 1 <= k <= m <= " + std::to_string(2 * (SMALL_MAX / 6)) +
+                    " (three blocks of m rounded up to even within " + std::to_string(SMALL_MAX) +
+                    " projected columns)");
+  if (bdg_status sd = check_device(plan)) return sd;
   cudaStream_t s = (cudaStream_t)stream;
   plan->last_stream = stream;
   memset(&plan->stats, 0, sizeof(plan->stats));

@@ -136,3 +136,8 @@ def test_binding_checks_blocks_before_the_library():
         p.biortho(torch.zeros((2, 3, 8), dtype=torch.float64), cpu)
     with pytest.raises(ValueError):
         p.solve(2, 4, X0=torch.zeros((4, 6, 8), dtype=torch.complex128), want_vectors=False)
+    # a locked pair needs both halves: Gl alone (or Fl alone) is refused
+    # rather than silently dropped
+    for kw in ({"Gl": cpu}, {"Fl": cpu}):
+        with pytest.raises(ValueError, match="Fl and Gl go together"):
+            p.biortho(cpu, cpu.clone(), **kw)

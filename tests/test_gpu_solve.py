@@ -110,10 +110,28 @@ def test_solve_rejects_bad_sizes():
     with pytest.raises(bdg.BdgError) as e:
         plan.solve(8, 200)
     assert e.value.status == bdg.ERR_UNSUPPORTED
-    # the largest block the header allows is 58; 59 is refused before any work
+    # the largest block the header allows is 52; 53 is refused before any work
     with pytest.raises(bdg.BdgError) as e:
-        plan.solve(8, 59)
-    assert e.value.status == bdg.ERR_UNSUPPORTED and "58" in str(e.value)
+        plan.solve(8, 53)
+    assert e.value.status == bdg.ERR_UNSUPPORTED and "52" in str(e.value)
+    plan.close()
+
+
+def test_solve_at_the_largest_block():
+    """A full solve with the largest block the header allows (m = 52), on a
+    2-D grid whose problem holds enough directions (16 x 16 x 3 f-side
+    unknowns): the basis reaches its 156-column maximum without overflowing
+    the projected eigensolver, and the pairs match the dense solution."""
+    torch = need_torch_cuda()
+    from paper_2506_08308_gb300 import bdg
+    import dataclasses
+    w = dataclasses.replace(W2, name="s2d_16_m52", k=30, m=52)
+    V, phi, mu, op = oracle_problem(w)
+    plan = make_plan(w, V, phi, prec=bdg.FP64, tol=1e-10, maxit=600)
+    X0 = torch.from_numpy(synth.random_block(w, w.m, complex_=True)).cuda()
+    om, UV, resid, nconv = plan.solve(w.k, w.m, X0=X0)
+    assert nconv == w.k
+    _check(w, op, om, UV.cpu().numpy().real, resid, w.k, _dense(op, w.k))
     plan.close()
 
 

@@ -46,6 +46,31 @@ def test_noalloc_matches_plan_mu(w):
     other.close()
 
 
+def test_noalloc_allocates_nothing():
+    """The entry point exists for callers that cannot let a call allocate (a
+    memory budget or caching allocator that owns all device memory, a loop
+    that cannot take an allocation's implicit synchronization), so the device's
+    free memory must not change across its calls on a fresh plan, whose own
+    lazily allocated scratch buffers are all still empty.  A first call on an
+    earlier plan comes before the measurement: loading the library's device
+    code (which holds the fixed array) is not an allocation by the call."""
+    torch = need_torch_cuda()
+    w = CASES[1]
+    V = synth.potential(w)
+    phi = _spinor(w)
+    warm = make_plan(w, V, phi)
+    mu_ref = warm.chemical_potentials_noalloc()
+    fresh = make_plan(w, V, phi, mu=(1.0, 2.0, 3.0))
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        np.testing.assert_allclose(fresh.chemical_potentials_noalloc(), mu_ref, rtol=1e-12, atol=0)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    warm.close()
+    fresh.close()
+
+
 def test_noalloc_vanishing_component():
     """A polar spinor (phi_1 = phi_-1 = 0): mu_+-1 come from mu_1 + mu_-1 = 2 mu_0."""
     need_torch_cuda()
