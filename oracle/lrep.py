@@ -220,7 +220,7 @@ def _vecs(X, P):
 
 
 def solve_iterative(op, k, m, X0, Zf, Zg, tol=1e-10, maxit=1000, sigma=None,
-                    rtol=1e-5, refresh_every=20, verbose=False):
+                    rtol=1e-5, refresh_every=20, verbose=False, inner=0):
     """Block structure-preserving subspace iteration (reading P8; after the
     LOBP4dCG family the paper cites for BOSP).  Real arithmetic.
 
@@ -235,6 +235,15 @@ def solve_iterative(op, k, m, X0, Zf, Zg, tol=1e-10, maxit=1000, sigma=None,
     T_sigma = IDFT (1/2|mu|^2 + sigma)^-1 DFT (reading P10).  The
     bi-orthonormalization keeps singular values >= rtol sigma_max (reading
     P16), and the images H X are recomputed every refresh_every iterations.
+
+    inner > 0 replaces T_sigma by that many steps of preconditioned conjugate
+    gradients (preconditioner T_sigma, start 0) on H_+ d_f = r_f over the
+    complement of Z_g, and on H_- d_g = r_g over the complement of Z_f (the
+    null spaces of H_+ and H_-, reading P7): an approximation of the exact
+    preconditioner (H_+^-1, H_-^-1) of the minimization principle, under
+    which the search space grows like block inverse iteration on H_- H_+
+    (reading P10; the paper names no preconditioner, and any one leaves the
+    converged pairs unchanged).
 
     X0: (m, 6, P) real FG start.  Returns (omega[k], F[k,3,P], G[k,3,P],
     resid[k], iterations)."""
@@ -256,6 +265,28 @@ def solve_iterative(op, k, m, X0, Zf, Zg, tol=1e-10, maxit=1000, sigma=None,
 
     def defl(X, Z):
         return X - Z @ (Z.T @ X) if Z.shape[1] else X
+
+    def pcg(hop, B, Z):
+        """inner steps of PCG for hop(X) = B, column by column, on Z^perp."""
+        B = defl(B, Z)
+        X = np.zeros_like(B)
+        R = B.copy()
+        Zr = defl(prec(R), Z)
+        D = Zr.copy()
+        rz = np.sum(R * Zr, 0)
+        for _ in range(inner):
+            HD = defl(hop(D), Z)
+            dhd = np.sum(D * HD, 0)
+            ok = dhd > 0
+            a = np.where(ok, rz / np.where(ok, dhd, 1.0), 0.0)
+            X = X + D * a
+            R = R - HD * a
+            Zr = defl(prec(R), Z)
+            rz_new = np.sum(R * Zr, 0)
+            b = np.where(rz != 0, rz_new / np.where(rz != 0, rz, 1.0), 0.0)
+            D = Zr + D * b
+            rz = rz_new
+        return X
 
     F = defl(_cols(np.asarray(X0)[:, :3], P), Zf)
     G = defl(_cols(np.asarray(X0)[:, 3:], P), Zg)
@@ -297,8 +328,12 @@ def solve_iterative(op, k, m, X0, Zf, Zg, tol=1e-10, maxit=1000, sigma=None,
         if mm >= k and np.all(resid[:k] <= tol):
             break
         act = np.nonzero(resid > tol)[0]
-        Df = defl(prec(Rf[:, act]), Zf)
-        Dg = defl(prec(Rg[:, act]), Zg)
+        if inner > 0:
+            Df = defl(pcg(hp, Rf[:, act], Zg), Zf)
+            Dg = defl(pcg(hm, Rg[:, act], Zf), Zg)
+        else:
+            Df = defl(prec(Rf[:, act]), Zf)
+            Dg = defl(prec(Rg[:, act]), Zg)
         Bf, Bg, HBf, HBg = Df, Dg, hp(Df), hm(Dg)
         if Pf is not None:
             Bf = np.concatenate([Bf, Pf[:, act]], 1)

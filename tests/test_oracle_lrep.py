@@ -169,6 +169,27 @@ def test_iterative_solver_matches_dense(ground):
     assert r.max() < 1e-9
 
 
+def test_iterative_solver_inner_pcg_matches_dense(ground):
+    """The subspace iteration with inner PCG on H_+ / H_- as preconditioner
+    (reading P10) reaches the same dense eigenpairs, on the 2-D workload's
+    physics on a 16^2 grid (q > 0, so Z_g is empty) and on Table 1's FM
+    instance (Z_g = span{-i S_y Phi}, H_+ singular)."""
+    import dataclasses
+    cases = [dataclasses.replace(synth.small(synth.W2D_N256, 16), name="pcg2d", k=10, m=16, block_seed=5),
+             synth.Workload("pcg_t1", (64,), (-16.0,), (16.0,), (1.0,), 885.4, -4.1, k=12, m=24, gs_seed=17,
+                            block_seed=18)]
+    for w in cases:
+        op, phi = _op(ground, w)
+        Zf, Zg = lrep.deflation_bases(op, phi)
+        X0 = synth.random_block(w, w.m, complex_=False)
+        om, F, G, res, it = lrep.solve_iterative(op, w.k, w.m, X0, Zf, Zg, tol=1e-10, maxit=400, inner=10)
+        assert res.max() <= 2e-10, (w.name, res)
+        om_d, _, _ = lrep.dense_solve_fg(op, w.k)
+        assert np.allclose(om, om_d, rtol=1e-9, atol=0), w.name
+        r = lrep.residual_uv(op, lrep.fg_to_uv(F, G), om)
+        assert r.max() < 1e-9
+
+
 def test_iterative_solver_table1_fm_case(ground):
     """The oracle's subspace iteration on the Table 1 FM case at h0/2
     (beta_n = 885.4, beta_s = -4.1: a ground state with full spin symmetry,
