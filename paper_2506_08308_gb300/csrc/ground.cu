@@ -126,7 +126,9 @@ __global__ void k_gs_maxres(const double2* __restrict__ hphi, const double2* __r
   if (threadIdx.x == 0) atomic_max_pos(out, m);
 }
 
-// up to 8 dot products over len complex elements (real parts): out[q] += sum a_q . b_q
+// up to 8 dot products over len complex elements (real parts), as per-CTA
+// partial sums out[q * gridDim.x + blockIdx.x] (summed in a fixed order on
+// the host, so that the flow is reproducible run to run)
 struct DotSet {
   const double2* a[8];
   const double2* b[8];
@@ -140,7 +142,7 @@ __global__ void k_gs_dots(DotSet d, long long len, double* out) {
          e += (long long)gridDim.x * blockDim.x)
       s += d.a[q][e].x * d.b[q][e].x;
     s = block_sum(s, red);
-    if (threadIdx.x == 0) atomicAdd(&out[q], s);
+    if (threadIdx.x == 0) out[(long long)q * gridDim.x + blockIdx.x] = s;
   }
 }
 
@@ -208,7 +210,8 @@ class GroundState {
         (st = alloc(&z_[0], sizeof(double2) * n3_)) || (st = alloc(&z_[1], sizeof(double2) * n3_)) ||
         (st = alloc(&cx_, sizeof(double2) * n3_)) || (st = alloc(&cr_, sizeof(double2) * n3_)) ||
         (st = alloc(&cz_, sizeof(double2) * n3_)) || (st = alloc(&cp_, sizeof(double2) * n3_)) ||
-        (st = alloc(&cap_, sizeof(double2) * n3_)) || (st = alloc(&dred_, sizeof(double) * 16)))
+        (st = alloc(&cap_, sizeof(double2) * n3_)) || (st = alloc(&dred_, sizeof(double) * 16)) ||
+        (st = alloc(&dpart_, sizeof(double) * DPART)))
       return st;
     BDG_CUDA_TRY(plan_, cudaMemcpyAsync(V_, V, sizeof(double) * np_, cudaMemcpyHostToDevice, s_));
     std::vector<double2> h(n3_);
@@ -284,11 +287,18 @@ class GroundState {
   }
 
   bdg_status dots(const DotSet& d, long long len, double* out) {
-    BDG_CUDA_TRY(plan_, cudaMemsetAsync(dred_, 0, sizeof(double) * 8, s_));
-    k_gs_dots<<<nblk(len), 256, 0, s_>>>(d, len, dred_);
+    const unsigned nb = nblk(len);
+    if ((size_t)nb * 8 > DPART) return fail(plan_, BDG_ERR_INVALID, "ground state: reduction grid too large");
+    k_gs_dots<<<nb, 256, 0, s_>>>(d, len, dpart_);
     BDG_CUDA_TRY(plan_, cudaGetLastError());
-    BDG_CUDA_TRY(plan_, cudaMemcpyAsync(out, dred_, sizeof(double) * d.count, cudaMemcpyDeviceToHost, s_));
+    hpart_.resize((size_t)nb * d.count);
+    BDG_CUDA_TRY(plan_, cudaMemcpyAsync(hpart_.data(), dpart_, sizeof(double) * hpart_.size(), cudaMemcpyDeviceToHost, s_));
     BDG_CUDA_TRY(plan_, cudaStreamSynchronize(s_));
+    for (int q = 0; q < d.count; ++q) {
+      double t = 0.0;
+      for (unsigned b = 0; b < nb; ++b) t += hpart_[(size_t)q * nb + b];
+      out[q] = t;
+    }
     return BDG_OK;
   }
   double2* comp(double2* v, int j) { return v + (long long)j * np_; }
@@ -536,6 +546,9 @@ class GroundState {
   int nz_ = 0;
   double2 *cx_ = nullptr, *cr_ = nullptr, *cz_ = nullptr, *cp_ = nullptr, *cap_ = nullptr;
   double* dred_ = nullptr;
+  static constexpr size_t DPART = 8 * 152 * 8;   // 8 sums x the largest reduction grid
+  double* dpart_ = nullptr;
+  std::vector<double> hpart_;
 };
 
 }  // namespace

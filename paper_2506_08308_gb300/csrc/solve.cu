@@ -37,6 +37,7 @@
 #include "blas.cuh"
 #include "common.cuh"
 #include "dense.cuh"
+#include "inner.cuh"
 #include "kdiag.cuh"
 #include "plan.cuh"
 
@@ -104,10 +105,12 @@ __global__ void k_unpack_uv(const typename CT<R>::T* __restrict__ bank, long lon
   }
 }
 
-// per real column: sum of squares over rows of a pair block (pair p, part s -> col 2p+s)
+// per real column: sum of squares over rows of a pair block (pair p, part s -> col 2p+s),
+// as partial sums per CTA row range: part[(p * gridDim.x + blockIdx.x) * 2 + s]
+constexpr int CN_BLOCKS = 64;
 template <typename R>
 __global__ void k_colnorm2(const typename CT<R>::T* __restrict__ A, long long ld, long long n, int pairs,
-                           double* __restrict__ out) {
+                           double* __restrict__ part) {
   __shared__ double red[2][32];
   const int p = blockIdx.y;
   double s0 = 0.0, s1 = 0.0;
@@ -126,9 +129,19 @@ __global__ void k_colnorm2(const typename CT<R>::T* __restrict__ A, long long ld
   if (threadIdx.x == 0) {
     double a = 0.0, b = 0.0;
     for (int q = 0; q < (int)blockDim.x / 32; ++q) { a += red[0][q]; b += red[1][q]; }
-    atomicAdd(&out[2 * p], a);
-    atomicAdd(&out[2 * p + 1], b);
+    part[((long long)p * gridDim.x + blockIdx.x) * 2] = a;
+    part[((long long)p * gridDim.x + blockIdx.x) * 2 + 1] = b;
   }
+}
+
+// out[2p + s] = sum of the nb partials of k_colnorm2 in a fixed order
+__global__ void k_colnorm_reduce(const double* __restrict__ part, int nb, int pairs, double* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= 2 * pairs) return;
+  const int p = c / 2, s = c - 2 * p;
+  double t = 0.0;
+  for (int b = 0; b < nb; ++b) t += part[((long long)p * nb + b) * 2 + s];
+  out[c] = t;
 }
 
 // scale the f-part of real column c by af[c] and the g-part by ag[c]
@@ -255,9 +268,26 @@ class Solver {
     for (int i = 0; i < NMAT; ++i) dmat_[i] = dsm_ + i * mat;
     dvec_ = dsm_ + NMAT * mat;
     dws_ = dvec_ + 64 * (size_t)big_;
+    if (alloc(&p, sizeof(double) * 2 * CN_BLOCKS * (size_t)cap_))
+      return fail(plan_, BDG_ERR_NOMEM, "column-norm workspace allocation failed");
+    cnpart_ = (double*)p;
     zf_ = (const T*)(sizeof(R) == 8 ? (const void*)plan_->zf64 : (const void*)plan_->zf32);
     zg_ = (const T*)(sizeof(R) == 8 ? (const void*)plan_->zg64 : (const void*)plan_->zg32);
+    if (inner_steps_ > 0) {
+      auto al = [this](void** q, size_t b) { return alloc(q, b); };
+      bdg_status st = inner_fp32_ ? in32_.init(plan_, mp_, al) : in64_.init(plan_, mp_, al);
+      if (st) return st;
+    }
     return BDG_OK;
+  }
+
+  // search directions D = (H_+^-1 r_f, H_-^-1 r_g) approximated by inner PCG
+  // in FP32 or FP64, or T_sigma r when the inner solver is off
+  bdg_status directions(T* W, int pairs) {
+    if (inner_steps_ <= 0) return precondition(W, W, pairs);
+    if (inner_fp32_) return in32_.template run<R>(W, W, pairs, inner_steps_, sigma_, s_);
+    if constexpr (sizeof(R) == 8) return in64_.template run<R>(W, W, pairs, inner_steps_, sigma_, s_);
+    return fail(plan_, BDG_ERR_INVALID, "an FP32 phase runs its inner solver in FP32");
   }
 
   // ---- block views ------------------------------------------------------
@@ -693,32 +723,45 @@ class Solver {
         const double* Qd = Qc + (size_t)nxb * ldc;
         if ((st = update_dev(fpart(U_[cur_], p0, pp), Pd, ldc, 0.0, fptr(Pb_, 0), mmp))) return st;
         if ((st = update_dev(gpart(U_[cur_], p0, pp), Qd, ldc, 0.0, gptr(Pb_, 0), mmp))) return st;
-        if ((st = update_dev(fpart(HU_[cur_], p0, pp), Pd, ldc, 0.0, fptr(HPb_, 0), mmp))) return st;
-        if ((st = update_dev(gpart(HU_[cur_], p0, pp), Qd, ldc, 0.0, gptr(HPb_, 0), mmp))) return st;
+        if (!exact_images_) {
+          if ((st = update_dev(fpart(HU_[cur_], p0, pp), Pd, ldc, 0.0, fptr(HPb_, 0), mmp))) return st;
+          if ((st = update_dev(gpart(HU_[cur_], p0, pp), Qd, ldc, 0.0, gptr(HPb_, 0), mmp))) return st;
+        }
         const size_t bytes = sizeof(T) * (size_t)vlen_ * mmp;
         BDG_CUDA_TRY(plan_, cudaMemcpyAsync(U_[nxt], Pb_, bytes, cudaMemcpyDeviceToDevice, s_));
-        BDG_CUDA_TRY(plan_, cudaMemcpyAsync(HU_[nxt], HPb_, bytes, cudaMemcpyDeviceToDevice, s_));
+        if (!exact_images_) BDG_CUDA_TRY(plan_, cudaMemcpyAsync(HU_[nxt], HPb_, bytes, cudaMemcpyDeviceToDevice, s_));
         if ((st = update_dev(fpart(U_[cur_], 0, p0), Pc, ldc, 1.0, fptr(U_[nxt], 0), mmp))) return st;
         if ((st = update_dev(gpart(U_[cur_], 0, p0), Qc, ldc, 1.0, gptr(U_[nxt], 0), mmp))) return st;
-        if ((st = update_dev(fpart(HU_[cur_], 0, p0), Pc, ldc, 1.0, fptr(HU_[nxt], 0), mmp))) return st;
-        if ((st = update_dev(gpart(HU_[cur_], 0, p0), Qc, ldc, 1.0, gptr(HU_[nxt], 0), mmp))) return st;
+        if (!exact_images_) {
+          if ((st = update_dev(fpart(HU_[cur_], 0, p0), Pc, ldc, 1.0, fptr(HU_[nxt], 0), mmp))) return st;
+          if ((st = update_dev(gpart(HU_[cur_], 0, p0), Qc, ldc, 1.0, gptr(HU_[nxt], 0), mmp))) return st;
+        }
       } else {
         // new Ritz block into the other bank
         if ((st = update_dev(fpart(U_[cur_], 0, pu), Pc, ldc, 0.0, fptr(U_[nxt], 0), mmp))) return st;
         if ((st = update_dev(gpart(U_[cur_], 0, pu), Qc, ldc, 0.0, gptr(U_[nxt], 0), mmp))) return st;
-        if ((st = update_dev(fpart(HU_[cur_], 0, pu), Pc, ldc, 0.0, fptr(HU_[nxt], 0), mmp))) return st;
-        if ((st = update_dev(gpart(HU_[cur_], 0, pu), Qc, ldc, 0.0, gptr(HU_[nxt], 0), mmp))) return st;
+        if (!exact_images_) {
+          if ((st = update_dev(fpart(HU_[cur_], 0, pu), Pc, ldc, 0.0, fptr(HU_[nxt], 0), mmp))) return st;
+          if ((st = update_dev(gpart(HU_[cur_], 0, pu), Qc, ldc, 0.0, gptr(HU_[nxt], 0), mmp))) return st;
+        }
       }
-      if (dbg_ && haveP) fprintf(stderr, "[bdg]   dbg P images after extraction %.3e\n", dbg_img(Pb_, HPb_, mmp));
+      if (dbg_ && haveP && !exact_images_)
+        fprintf(stderr, "[bdg]   dbg P images after extraction %.3e\n", dbg_img(Pb_, HPb_, mmp));
       cur_ = nxt;
       T* X = U_[cur_];
       T* HX = HU_[cur_];
+      if (exact_images_) {
+        // images of the new Ritz block by the product itself: every residual
+        // and every projected matrix then holds to the rounding of one product
+        if ((st = apply_fg(X, HX, mmp))) return st;
+        refreshed_at = it;
+      }
       // The images HX are carried by linear combination; their rounding
       // drifts slowly away from H X.  Recompute them exactly every 20
       // iterations and before a convergence claim is accepted.  (A refresh
       // on every stall dropped the previous-update block P again and again
       // near the floor and could keep the iteration from recovering.)
-      const bool refresh = refresh_next || (it > 0 && it % 20 == 0);
+      const bool refresh = !exact_images_ && (refresh_next || (it > 0 && it % 20 == 0));
       if (refresh) {
         if ((st = apply_fg(X, HX, mmp))) return st;
         haveP = false;  // P's images were drifted the same way
@@ -789,7 +832,7 @@ class Solver {
         if (worst < 0.7 * best) {
           best = worst;
           stall = 0;
-        } else if (++stall >= 6) {
+        } else if (++stall >= fp32_stall_) {
           return BDG_OK;
         }
       }
@@ -812,7 +855,8 @@ class Solver {
         nu = mm;
         continue;
       }
-      if (dbg_ && haveP) fprintf(stderr, "[bdg]   dbg P images before gather %.3e\n", dbg_img(Pb_, HPb_, mmp));
+      if (dbg_ && haveP && !exact_images_)
+        fprintf(stderr, "[bdg]   dbg P images before gather %.3e\n", dbg_img(Pb_, HPb_, mmp));
       if (dbg_ && haveP) {
         // gather check on a copy: G = P Sel must equal the selected columns
         HostMat Sel2(2 * mmp, 2 * nap);
@@ -830,13 +874,13 @@ class Solver {
       HostMat Sel(2 * mmp, 2 * nap);
       for (int jj = 0; jj < na; ++jj) Sel(act[jj], jj) = 1.0;
       if ((st = update_full(Rb_, mmp, Sel, Wb_, nap))) return st;
-      if ((st = precondition(Wb_, Wb_, nap))) return st;
+      if ((st = directions(Wb_, nap))) return st;
       if ((st = deflate(Wb_, 0, nap))) return st;
       // unit f- and g-parts before the product: the two real columns sharing
       // a complex vector then have equal norms, so the rounding crosstalk
       // between them in the FFTs stays at eps relative to each column
       if ((st = normalize_parts(Wb_, nullptr, nap))) return st;
-      if ((st = apply_fg(Wb_, HWb_, nap))) return st;
+      if (!exact_images_ && (st = apply_fg(Wb_, HWb_, nap))) return st;
       int nw = 2 * nap;
       if (haveP) {
         // previous-update columns that carry information: |P_j| >= 1e-12 |X_j|
@@ -852,7 +896,7 @@ class Solver {
           HostMat SelP(2 * mmp, 2 * nap);
           for (int jj = 0; jj < npa; ++jj) SelP(actp[jj], jj) = 1.0;
           if ((st = update_full(Pb_, mmp, SelP, Wb_ + (long long)nap * vlen_, nap))) return st;
-          if ((st = update_full(HPb_, mmp, SelP, HWb_ + (long long)nap * vlen_, nap))) return st;
+          if (!exact_images_ && (st = update_full(HPb_, mmp, SelP, HWb_ + (long long)nap * vlen_, nap))) return st;
           nw = 4 * nap;
         }
       }
@@ -861,19 +905,24 @@ class Solver {
       // Each block holds at most 2 nap columns, so its Jordan-Wielandt
       // problem stays within the projected solver's size.
       int rp = 0;
+      T* const HWx = exact_images_ ? nullptr : HWb_;   // images carried only without exact products
       if (nw > 2 * nap) {
         T* WP = Wb_ + (long long)nap * vlen_;
-        T* HWP = HWb_ + (long long)nap * vlen_;
+        T* HWP = HWx ? HWx + (long long)nap * vlen_ : nullptr;
         if ((st = cgs2(X, HX, mmp, WP, HWP, nap))) return st;
-        if ((st = biortho_block(WP, HWP, nap, 2 * nap, fptr(X, mmp), fptr(HX, mmp), rtol_, &rp))) return st;
+        if ((st = biortho_block(WP, HWP, nap, 2 * nap, fptr(X, mmp), HWP ? fptr(HX, mmp) : nullptr, rtol_, &rp)))
+          return st;
       }
       const int rpp = (rp + 1) / 2;
-      if ((st = cgs2(X, HX, mmp + rpp, Wb_, HWb_, nap))) return st;
+      if ((st = cgs2(X, HX, mmp + rpp, Wb_, HWx, nap))) return st;
       int rd = 0;
-      if ((st = biortho_block(Wb_, HWb_, nap, 2 * nap, fptr(X, mmp + rpp), fptr(HX, mmp + rpp), rtol_, &rd)))
+      if ((st = biortho_block(Wb_, HWx, nap, 2 * nap, fptr(X, mmp + rpp), HWx ? fptr(HX, mmp + rpp) : nullptr,
+                              rtol_, &rd)))
         return st;
       if (log_) fprintf(stderr, "[bdg]   block ranks P %d D %d\n", rp, rd);
       if (rp + rd == 0) return fail(plan_, BDG_ERR_BREAKDOWN, "search directions lost rank");
+      // images of the new basis columns [P', D'] by one product
+      if (exact_images_ && (st = apply_fg(fptr(X, mmp), fptr(HX, mmp), rpp + (rd + 1) / 2))) return st;
       nxb = 2 * mmp;
       nu = 2 * (mmp + rpp) + rd;
     }
@@ -891,9 +940,9 @@ class Solver {
       if ((st = gram(gpart(Bk, 0, bp), fpart(W, 0, wp), c1))) return st;
       if ((st = gram(fpart(Bk, 0, bp), gpart(W, 0, wp), c2))) return st;
       if ((st = update_dev(fpart(Bk, 0, bp), c1, nw, 1.0, fptr(W, 0), wp, -1.0))) return st;
-      if ((st = update_dev(fpart(HBk, 0, bp), c1, nw, 1.0, fptr(HW, 0), wp, -1.0))) return st;
+      if (HW && (st = update_dev(fpart(HBk, 0, bp), c1, nw, 1.0, fptr(HW, 0), wp, -1.0))) return st;
       if ((st = update_dev(gpart(Bk, 0, bp), c2, nw, 1.0, gptr(W, 0), wp, -1.0))) return st;
-      if ((st = update_dev(gpart(HBk, 0, bp), c2, nw, 1.0, gptr(HW, 0), wp, -1.0))) return st;
+      if (HW && (st = update_dev(gpart(HBk, 0, bp), c2, nw, 1.0, gptr(HW, 0), wp, -1.0))) return st;
     }
     return BDG_OK;
   }
@@ -930,21 +979,28 @@ class Solver {
   }
 
   // per real column: squared norm of the f-part (part 0) or the g-part (part 1)
+  // squared column norms over n rows from offset off of each 6-field column,
+  // reduced in a fixed order (the solve is reproducible run to run)
+  bdg_status colnorm_dev(const T* bank, long long n, int pairs, double* d) {
+    if (pairs > cap_) return fail(plan_, BDG_ERR_INVALID, "column-norm block wider than its workspace");
+    k_colnorm2<R><<<dim3(CN_BLOCKS, pairs), 256, 0, s_>>>(bank, vlen_, n, pairs, cnpart_);
+    BDG_CUDA_TRY(plan_, cudaGetLastError());
+    k_colnorm_reduce<<<(2 * pairs + 127) / 128, 128, 0, s_>>>(cnpart_, CN_BLOCKS, pairs, d);
+    BDG_CUDA_TRY(plan_, cudaGetLastError());
+    return BDG_OK;
+  }
+
   bdg_status colnorms_part(const T* bank, int pairs, int part, std::vector<double>& out) {
     double* d = dvec_ + 10 * big_;
-    BDG_CUDA_TRY(plan_, cudaMemsetAsync(d, 0, sizeof(double) * 2 * pairs, s_));
-    dim3 grid(64, pairs);
-    k_colnorm2<R><<<grid, 256, 0, s_>>>(bank + (part ? n3_ : 0), vlen_, n3_, pairs, d);
-    BDG_CUDA_TRY(plan_, cudaGetLastError());
+    bdg_status st = colnorm_dev(bank + (part ? n3_ : 0), n3_, pairs, d);
+    if (st) return st;
     return download(d, out, 2 * pairs);
   }
 
   bdg_status colnorms(const T* bank, int pairs, std::vector<double>& out) {
     double* d = dvec_ + 6 * big_;
-    BDG_CUDA_TRY(plan_, cudaMemsetAsync(d, 0, sizeof(double) * 2 * pairs, s_));
-    dim3 grid(64, pairs);
-    k_colnorm2<R><<<grid, 256, 0, s_>>>(bank, vlen_, vlen_, pairs, d);
-    BDG_CUDA_TRY(plan_, cudaGetLastError());
+    bdg_status st = colnorm_dev(bank, vlen_, pairs, d);
+    if (st) return st;
     out.assign(2 * pairs, 0.0);
     BDG_CUDA_TRY(plan_, cudaMemcpyAsync(out.data(), d, sizeof(double) * 2 * pairs, cudaMemcpyDeviceToHost, s_));
     BDG_CUDA_TRY(plan_, cudaStreamSynchronize(s_));
@@ -983,14 +1039,28 @@ class Solver {
   double* dmat_[NMAT] = {};
   double* dvec_ = nullptr;
   double* dws_ = nullptr;
+  double* cnpart_ = nullptr;
   int big_ = 0;
   bool dbg_eigh_ = getenv("BDG_CHECK_EIGH") != nullptr;
   T* dbg_buf_ = nullptr;
   std::vector<void*> owned_;
   int cur_ = 0, nx_ = 0, mm_ = 0;
   double sigma_ = 1.0;
+  // inner PCG steps per search direction (0: the kinetic preconditioner
+  // alone); set per precision by bdg_solve
+  int inner_steps_ = 10;
+  bool inner_fp32_ = sizeof(R) == 4;
+  InnerPCG<float> in32_;
+  InnerPCG<double> in64_;
   double rtol_ = 1e-10;
   double zero_tol2_ = 1e-12;
+  // images H X of the Ritz block and of new basis columns by the product
+  // itself (otherwise carried by linear combination, refreshed every 20
+  // iterations; carried images drift by eps |coefficients| and stall strong
+  // search directions near 1e-7)
+  bool exact_images_ = getenv("BDG_CARRY_IMAGES") == nullptr;
+  // the FP32 phase hands over after this many iterations without a 30 % gain
+  int fp32_stall_ = getenv("BDG_FP32_STALL") ? atoi(getenv("BDG_FP32_STALL")) : 1;
   bool log_ = getenv("BDG_LOG") != nullptr;
   std::vector<double> omega_, resid_;
 };
@@ -1069,14 +1139,25 @@ bdg_status bdg_solve(bdg_plan_t plan, int k, int m, const void* X0, double* omeg
   int it1 = 0, it2 = 0;
   Solver<double> S64(plan, s, m);
   S64.sigma_ = sigma;
-  S64.rtol_ = 1e-5;
+  // rank cut of the bi-orthonormalization: a kept direction with singular
+  // value sigma scales the projected matrices by 1 / sigma, and FP64 rounding
+  // with it; 1e-5 stalled strong search directions between 1e-7 and 1e-6,
+  // 1e-4 ... 1e-2 converged alike (reading P16)
+  S64.rtol_ = getenv("BDG_RTOL64") ? atof(getenv("BDG_RTOL64")) : 1e-3;
+  S64.inner_fp32_ = plan->prm.prec == BDG_MIXED;   // plain FP64 keeps every kernel in FP64
+  // inner steps: each precision at its fastest measured setting on the 2-D
+  // 256^2 workload (FP64 inner products cost about twenty FP32 ones)
+  const char* env_inner = getenv("BDG_INNER_STEPS");
+  S64.inner_steps_ = env_inner ? atoi(env_inner) : (S64.inner_fp32_ ? 12 : 8);
   if (plan->prm.prec == BDG_MIXED) {
     Solver<float> S32(plan, s, m);
     S32.sigma_ = sigma;
     S32.rtol_ = 1e-4;
+    S32.inner_steps_ = env_inner ? atoi(env_inner) : 12;
     if ((st = S32.init_buffers())) return st;
     if ((st = S32.start_random(X0, plan->prm.seed))) return st;
-    if ((st = S32.iterate(k, tol, maxit, 3e-4, &it1, &conv))) return st;
+    const double floor32 = getenv("BDG_FP32_FLOOR") ? atof(getenv("BDG_FP32_FLOOR")) : 3e-4;
+    if ((st = S32.iterate(k, tol, maxit, floor32, &it1, &conv))) return st;
     if ((st = S64.init_buffers())) return st;
     if ((st = transfer(S32, S64, s))) return st;
   } else {
