@@ -1,6 +1,8 @@
 // Small dense FP64 kernels: GEMM, symmetric eigen-decomposition (FP32
 // Jacobi + FP64 Ogita-Aishima refinement), scaling.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <vector>
 
@@ -321,6 +323,192 @@ size_t eigh_workspace_doubles(int n) { return (size_t)48 * n * n + 128 * n + 256
 
 namespace {
 
+// ---------------------------------------------------------------------------
+// All clusters of an FP32 Jacobi basis resolved in one launch.  CTA b takes
+// the run of columns [start, start + size) of V (n x n, ld n) with midpoint
+// shift c: two FP64 Newton-Schulz steps orthonormalize the columns, the
+// shifted projection G = Vs^T (A - c I) Vs (norm about half the run's
+// spread) is diagonalized by parallel cyclic Jacobi in FP64 (rotations of
+// Golub & Van Loan, round-robin pairs as in k_jacobi), and the rotated
+// columns and eigenvalues (ascending within the run) replace the old ones.
+// ---------------------------------------------------------------------------
+constexpr int RC_MAX_CLUSTERS = 96;   // runs of two or more columns: at most n / 2
+constexpr int RC_NS_MAX = 48;         // wider runs keep the sequential path
+struct ClusterList {
+  int count;
+  int start[RC_MAX_CLUSTERS];
+  int size[RC_MAX_CLUSTERS];
+  double shift[RC_MAX_CLUSTERS];
+};
+
+size_t resolve_smem_bytes(int n, int ns) {
+  const int np2 = (ns + 1) & ~1;
+  return sizeof(double) * (2 * (size_t)n * ns + 2 * (size_t)ns * ns + 2 * (size_t)np2 + 64) +
+         sizeof(int) * ((size_t)np2 + 2 * (size_t)ns + 8);
+}
+
+__global__ void __launch_bounds__(256) k_resolve_clusters(int n, const double* __restrict__ A, int lda,
+                                                          double* __restrict__ w, double* __restrict__ V,
+                                                          ClusterList cl) {
+  extern __shared__ double rsm[];
+  const int i0 = cl.start[blockIdx.x], ns = cl.size[blockIdx.x];
+  const double c = cl.shift[blockIdx.x];
+  const int np2 = (ns + 1) & ~1, npair = np2 / 2;
+  double* Vs = rsm;                       // [n][ns]
+  double* T = Vs + (size_t)n * ns;        // [n][ns]
+  double* G = T + (size_t)n * ns;         // [ns][ns]
+  double* Z = G + (size_t)ns * ns;        // [ns][ns]
+  double* cs = Z + (size_t)ns * ns;       // [npair][2]
+  double* red = cs + np2;                 // [64]
+  int* pq = reinterpret_cast<int*>(red + 64);   // [npair][2]
+  int* rank = pq + np2;                   // [ns]
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < n * ns; e += nt) {
+    const int i = e / ns, j = e - i * ns;
+    Vs[e] = V[(long long)i * n + i0 + j];
+  }
+  __syncthreads();
+  // Vs <- Vs (3 I - Vs^T Vs) / 2, twice
+  for (int it = 0; it < 2; ++it) {
+    for (int e = tid; e < ns * ns; e += nt) {
+      const int a = e / ns, b = e - a * ns;
+      double sacc = 0.0;
+      for (int i = 0; i < n; ++i) sacc = fma(Vs[i * ns + a], Vs[i * ns + b], sacc);
+      G[e] = (a == b ? 1.5 : 0.0) - 0.5 * sacc;
+    }
+    __syncthreads();
+    for (int e = tid; e < n * ns; e += nt) {
+      const int i = e / ns, b = e - i * ns;
+      double sacc = 0.0;
+      for (int a = 0; a < ns; ++a) sacc = fma(Vs[i * ns + a], G[a * ns + b], sacc);
+      T[e] = sacc;
+    }
+    __syncthreads();
+    for (int e = tid; e < n * ns; e += nt) Vs[e] = T[e];
+    __syncthreads();
+  }
+  // T = (A - c I) Vs, G = Vs^T T symmetrized
+  for (int e = tid; e < n * ns; e += nt) {
+    const int i = e / ns, b = e - i * ns;
+    const double* Ai = A + (long long)i * lda;
+    double sacc = -c * Vs[i * ns + b];
+    for (int k = 0; k < n; ++k) sacc = fma(Ai[k], Vs[k * ns + b], sacc);
+    T[e] = sacc;
+  }
+  __syncthreads();
+  for (int e = tid; e < ns * ns; e += nt) {
+    const int a = e / ns, b = e - a * ns;
+    double sacc = 0.0;
+    for (int i = 0; i < n; ++i) sacc = fma(Vs[i * ns + a], T[i * ns + b], sacc);
+    Z[e] = sacc;
+  }
+  __syncthreads();
+  double fro = 0.0;
+  for (int e = tid; e < ns * ns; e += nt) {
+    const int a = e / ns, b = e - a * ns;
+    const double v = 0.5 * (Z[a * ns + b] + Z[b * ns + a]);
+    G[e] = v;
+    fro += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
+  if ((tid & 31) == 0) red[tid >> 5] = fro;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (nt + 31) / 32; ++q) t += red[q];
+    red[32] = sqrt(t);
+  }
+  for (int e = tid; e < ns * ns; e += nt) Z[e] = (e / ns == e % ns) ? 1.0 : 0.0;
+  __syncthreads();
+  const double tiny = 1e-18 * red[32];
+  // parallel cyclic Jacobi in FP64
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0.0;
+    for (int e = tid; e < ns * ns; e += nt) {
+      const int a = e / ns, b = e - a * ns;
+      if (a != b) off += G[e] * G[e];
+    }
+    for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = off;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int q = 0; q < (nt + 31) / 32; ++q) t += red[q];
+      red[33] = t;
+    }
+    __syncthreads();
+    if (!(red[33] > 1e-32 * red[32] * red[32]) || !(red[33] > tiny * tiny)) break;
+    for (int r = 0; r < np2 - 1; ++r) {
+      if (tid < npair) {
+        const int k = tid;
+        int p = (r + k) % (np2 - 1);
+        int q = (k == 0) ? (np2 - 1) : (r - k + np2 - 1) % (np2 - 1);
+        if (p > q) { const int t = p; p = q; q = t; }
+        double cc = 1.0, ss = 0.0;
+        if (q < ns) {
+          const double apq = G[p * ns + q], app = G[p * ns + p], aqq = G[q * ns + q];
+          if (fabs(apq) > tiny) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            cc = 1.0 / sqrt(1.0 + t * t);
+            ss = t * cc;
+          }
+        } else {
+          q = p;
+        }
+        pq[2 * k] = p;
+        pq[2 * k + 1] = q;
+        cs[2 * k] = cc;
+        cs[2 * k + 1] = ss;
+      }
+      __syncthreads();
+      const int nblk = npair * npair;
+      for (int e = tid; e < nblk + npair * ns; e += nt) {
+        if (e < nblk) {
+          const int k = e / npair, l = e - k * npair;
+          const int p = pq[2 * k], q = pq[2 * k + 1], u = pq[2 * l], v = pq[2 * l + 1];
+          const double ck = cs[2 * k], sk = cs[2 * k + 1], cl_ = cs[2 * l], sl = cs[2 * l + 1];
+          const double x00 = G[p * ns + u], x01 = G[p * ns + v], x10 = G[q * ns + u], x11 = G[q * ns + v];
+          const double r00 = ck * x00 - sk * x10, r01 = ck * x01 - sk * x11;
+          const double r10 = sk * x00 + ck * x10, r11 = sk * x01 + ck * x11;
+          G[p * ns + u] = cl_ * r00 - sl * r01;
+          G[p * ns + v] = sl * r00 + cl_ * r01;
+          G[q * ns + u] = cl_ * r10 - sl * r11;
+          G[q * ns + v] = sl * r10 + cl_ * r11;
+        } else {
+          const int f = e - nblk, l = f / ns, i = f - l * ns;
+          const int u = pq[2 * l], v = pq[2 * l + 1];
+          if (u == v) continue;
+          const double cl_ = cs[2 * l], sl = cs[2 * l + 1];
+          const double zp = Z[i * ns + u], zq = Z[i * ns + v];
+          Z[i * ns + u] = cl_ * zp - sl * zq;
+          Z[i * ns + v] = sl * zp + cl_ * zq;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // ascending order within the run, new columns Vs Z, eigenvalues + c
+  for (int j = tid; j < ns; j += nt) {
+    const double dj = G[j * ns + j];
+    int rk = 0;
+    for (int l = 0; l < ns; ++l) {
+      const double dl = G[l * ns + l];
+      rk += (dl < dj) || (dl == dj && l < j);
+    }
+    rank[j] = rk;
+    w[i0 + rk] = dj + c;
+  }
+  __syncthreads();
+  for (int e = tid; e < n * ns; e += nt) {
+    const int i = e / ns, j = e - i * ns;
+    double sacc = 0.0;
+    for (int a = 0; a < ns; ++a) sacc = fma(Vs[i * ns + a], Z[a * ns + j], sacc);
+    V[(long long)i * n + i0 + rank[j]] = sacc;
+  }
+}
+
 // FP32 Jacobi start for A (n x n, lda) into (w, V), with clusters resolved
 // by recursion.  FP32 separates eigenvalues only down to about 1e-7 max|w|;
 // every run of consecutive eigenvalues closer than 1e-4 max|w| (a cluster
@@ -334,8 +522,24 @@ cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double
                     sizeof(int) * 2 * (n / 2 + 1) + sizeof(float) * 64;
   cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
+  static const bool prof = getenv("BDG_PROFILE_EIGH") != nullptr;
+  cudaEvent_t pj[2] = {};
+  if (prof) {
+    cudaEventCreate(&pj[0]);
+    cudaEventCreate(&pj[1]);
+    cudaEventRecord(pj[0], s);
+  }
   k_jacobi<<<1, 1024, sm, s>>>(n, A, lda, w, V, 30);
   if ((e = cudaGetLastError())) return e;
+  if (prof) {
+    cudaEventRecord(pj[1], s);
+    cudaEventSynchronize(pj[1]);
+    float t = 0;
+    cudaEventElapsedTime(&t, pj[0], pj[1]);
+    fprintf(stderr, "[bdg]   jacobi n %d depth %d %.3f ms\n", n, depth, t);
+    cudaEventDestroy(pj[0]);
+    cudaEventDestroy(pj[1]);
+  }
   if (depth >= 4 || n < 2) return cudaSuccess;
   std::vector<double> hw(n);
   if ((e = cudaMemcpyAsync(hw.data(), w, sizeof(double) * n, cudaMemcpyDeviceToHost, s))) return e;
@@ -345,6 +549,11 @@ cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double
   if (!(amax > 0)) return cudaSuccess;
   if (depth == 0) floor *= amax;   // the caller's floor is relative at the top level
   const double tau = 1e-4 * amax;
+  // at the top level the runs of at most RC_NS_MAX columns are resolved by one
+  // launch (FP64 Jacobi per run); wider runs, and deeper levels, re-solve in turn
+  ClusterList cl;
+  cl.count = 0;
+  int ns_max = 0;
   for (int i0 = 0; i0 < n;) {
     int i1 = i0 + 1;
     while (i1 < n && hw[i1] - hw[i1 - 1] < tau) ++i1;
@@ -358,7 +567,14 @@ cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double
     // runs whose eigenvalues all lie below the caller's floor (|lambda| of the
     // original matrix) are not needed resolved: the caller discards them
     const double top = std::max(std::fabs(hw[i0] + shift), std::fabs(hw[i1 - 1] + shift));
-    if (ns >= 2 && spread > 0 && !degenerate && !(top < floor)) {
+    if (ns >= 2 && spread > 0 && !degenerate && !(top < floor) && depth == 0 && ns <= RC_NS_MAX &&
+        cl.count < RC_MAX_CLUSTERS) {
+      cl.start[cl.count] = i0;
+      cl.size[cl.count] = ns;
+      cl.shift[cl.count] = 0.5 * (hw[i0] + hw[i1 - 1]);
+      cl.count++;
+      ns_max = std::max(ns_max, ns);
+    } else if (ns >= 2 && spread > 0 && !degenerate && !(top < floor)) {
       const double c = 0.5 * (hw[i0] + hw[i1 - 1]);  // midpoint: the shifted norm is half the spread
       double* Vs = ws;                         // n x ns
       double* AVs = Vs + (size_t)n * ns;       // n x ns
@@ -397,6 +613,12 @@ cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double
     }
     i0 = i1;
   }
+  if (cl.count > 0) {
+    const size_t smr = resolve_smem_bytes(n, ns_max);
+    if ((e = cudaFuncSetAttribute(k_resolve_clusters, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr))) return e;
+    k_resolve_clusters<<<cl.count, 256, smr, s>>>(n, A, lda, w, V, cl);
+    if ((e = cudaGetLastError())) return e;
+  }
   return cudaSuccess;
 }
 
@@ -426,12 +648,20 @@ cudaError_t eigh(int n, const double* A, int lda, double* w, double* V, double* 
   double* lam2 = lam + n;         // n
   double* anorm = lam2 + n;       // 8
   double* rest = anorm + 8;
+  // diagnostics (BDG_PROFILE_EIGH): device time of the start, the refinement
+  // and the ordering of this call, printed per call
+  static const bool prof = getenv("BDG_PROFILE_EIGH") != nullptr;
+  cudaEvent_t pe[4] = {};
+  if (prof)
+    for (auto& x : pe) cudaEventCreate(&x);
+  if (prof) cudaEventRecord(pe[0], s);
   if (from_identity) {
     k_identity_start<<<(n * n + 255) / 256, 256, 0, s>>>(n, A, lda, X, lam2);
     if ((e = cudaGetLastError())) return e;
   } else if ((e = jacobi_multilevel(n, A, lda, lam2, X, rest, 0, floor_rel, 0.0, s))) {
     return e;
   }
+  if (prof) cudaEventRecord(pe[1], s);
   k_frob<<<1, 1024, 0, s>>>(n, A, lda, anorm);
   double* cur = X;
   double* nxt = X2;
@@ -456,7 +686,19 @@ cudaError_t eigh(int n, const double* A, int lda, double* w, double* V, double* 
     if ((e = dgemm_small(false, false, n, n, n, 1.0, cur, n, R, n, 0.0, nxt, n, s))) return e;
     double* t = cur; cur = nxt; nxt = t;
   }
+  if (prof) cudaEventRecord(pe[2], s);
   k_sort_eig<<<1, 256, 0, s>>>(n, refine_steps > 0 ? lam : lam2, cur, w, V);
+  if (prof) {
+    cudaEventRecord(pe[3], s);
+    cudaEventSynchronize(pe[3]);
+    float t0 = 0, t1 = 0, t2 = 0;
+    cudaEventElapsedTime(&t0, pe[0], pe[1]);
+    cudaEventElapsedTime(&t1, pe[1], pe[2]);
+    cudaEventElapsedTime(&t2, pe[2], pe[3]);
+    fprintf(stderr, "[bdg] eigh n %d %s start %.3f refine %.3f sort %.3f ms\n", n, from_identity ? "identity" : "jacobi",
+            t0, t1, t2);
+    for (auto& x : pe) cudaEventDestroy(x);
+  }
   return cudaGetLastError();
 }
 

@@ -271,6 +271,11 @@ class Solver {
     if (alloc(&p, sizeof(double) * 2 * CN_BLOCKS * (size_t)cap_))
       return fail(plan_, BDG_ERR_NOMEM, "column-norm workspace allocation failed");
     cnpart_ = (double*)p;
+    if (cudaMallocHost((void**)&pinned_, sizeof(double) * PIN_DOUBLES) != cudaSuccess) {
+      cudaGetLastError();
+      pinned_ = nullptr;
+      return fail(plan_, BDG_ERR_NOMEM, "pinned staging allocation failed");
+    }
     zf_ = (const T*)(sizeof(R) == 8 ? (const void*)plan_->zf64 : (const void*)plan_->zf32);
     zg_ = (const T*)(sizeof(R) == 8 ? (const void*)plan_->zg64 : (const void*)plan_->zg32);
     if (inner_steps_ > 0) {
@@ -317,7 +322,8 @@ class Solver {
   bdg_status update(const PairBlock<R>& A, const HostMat& C, double beta, T* y, int Q) {
     if (Q == 0) return BDG_OK;
     double* dC = dmat_[MAT_HOST];
-    BDG_CUDA_TRY(plan_, cudaMemcpyAsync(dC, C.a.data(), sizeof(double) * C.a.size(), cudaMemcpyHostToDevice, s_));
+    bdg_status st = upload(dC, C.a.data(), C.a.size());
+    if (st) return st;
     return update_dev(A, dC, C.c, beta, y, Q);
   }
   bdg_status apply_fg(const T* x, T* y, int pairs) {
@@ -342,16 +348,42 @@ class Solver {
     BDG_CUDA_TRY(plan_, kdiag_launch<R>(g));
     return BDG_OK;
   }
-  bdg_status download(const double* d, std::vector<double>& h, size_t n) {
-    h.assign(n, 0.0);
-    BDG_CUDA_TRY(plan_, cudaMemcpyAsync(h.data(), d, sizeof(double) * n, cudaMemcpyDeviceToHost, s_));
+  // Host <-> device copies of small data go through a pinned staging arena:
+  // a copy from pageable memory would make the stream drain first.  Staged
+  // uploads stay queued behind the work in flight; the arena is recycled at
+  // every point where the host waits for the stream anyway.
+  bdg_status sync_stream() {
     BDG_CUDA_TRY(plan_, cudaStreamSynchronize(s_));
+    pin_off_ = 0;
     return BDG_OK;
   }
-  bdg_status upload(double* d, const std::vector<double>& h) {
-    BDG_CUDA_TRY(plan_, cudaMemcpyAsync(d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, s_));
+  double* stage(size_t n) {
+    if (pin_off_ + n > PIN_DOUBLES) {
+      if (sync_stream()) return nullptr;
+      if (n > PIN_DOUBLES) return nullptr;
+    }
+    double* p = pinned_ + pin_off_;
+    pin_off_ += (n + 7) & ~(size_t)7;
+    return p;
+  }
+  bdg_status download(const double* d, std::vector<double>& h, size_t n) {
+    double* p = stage(n);
+    if (!p) return fail(plan_, BDG_ERR_INVALID, "staging arena too small for a download");
+    BDG_CUDA_TRY(plan_, cudaMemcpyAsync(p, d, sizeof(double) * n, cudaMemcpyDeviceToHost, s_));
+    bdg_status st = sync_stream();
+    if (st) return st;
+    h.assign(p, p + n);
     return BDG_OK;
   }
+  bdg_status upload(double* d, const double* h, size_t n) {
+    if (n == 0) return BDG_OK;
+    double* p = stage(n);
+    if (!p) return fail(plan_, BDG_ERR_INVALID, "staging arena too small for an upload");
+    memcpy(p, h, sizeof(double) * n);
+    BDG_CUDA_TRY(plan_, cudaMemcpyAsync(d, p, sizeof(double) * n, cudaMemcpyHostToDevice, s_));
+    return BDG_OK;
+  }
+  bdg_status upload(double* d, const std::vector<double>& h) { return upload(d, h.data(), h.size()); }
   // Gram of real columns, leading na x nb block copied to the host
   bdg_status gram_host(const PairBlock<R>& A, int na, const PairBlock<R>& B, int nb, HostMat& out) {
     double* G = dmat_[MAT_G1];
@@ -373,7 +405,10 @@ class Solver {
   bdg_status eigh_dev(int n, const double* A, int lda, double* dw, double* dV, std::vector<double>& w,
                       double floor_rel = 0.0, bool from_identity = false) {
     if (n > SMALL_MAX) return fail(plan_, BDG_ERR_UNSUPPORTED, "projected problem larger than supported");
+    int si_;
+    cudaEvent_t se_ = sec_begin(from_identity ? "  eigh (identity start)" : (n > 100 ? "  eigh n>100" : "  eigh n<=100"), &si_);
     bdg_status st = cuda(eigh(n, A, lda, dw, dV, dws_, 3, s_, floor_rel, from_identity), "eigh");
+    sec_end(se_);
     if (st) return st;
     if ((st = download(dw, w, n))) return st;
     if (dbg_eigh_) check_eigh(n, A, lda, dV, w);
@@ -639,8 +674,10 @@ class Solver {
     }
     double* Kp = dmat_[MAT_G1];
     double* Km = dmat_[MAT_G2];
-    if ((st = gram(fpart(U, 0, pu), fpart(HU, 0, pu), Kp))) return st;
-    if ((st = gram(gpart(U, 0, pu), gpart(HU, 0, pu), Km))) return st;
+    { int si_; cudaEvent_t se_ = sec_begin("  RR grams", &si_);
+      st = gram(fpart(U, 0, pu), fpart(HU, 0, pu), Kp);
+      if (!st) st = gram(gpart(U, 0, pu), gpart(HU, 0, pu), Km);
+      sec_end(se_); if (st) return st; }
     if ((st = cuda(dsym_small(nu, Kp, ldg, s_), "sym")) || (st = cuda(dsym_small(nu, Km, ldg, s_), "sym")))
       return st;
     // stage 1
@@ -705,7 +742,10 @@ class Solver {
       plan_->stats.iterations++;
       if (sizeof(R) == 4) plan_->stats.iterations_fp32++;
       std::vector<double> om;
+      int si_rr;
+      cudaEvent_t se_rr = sec_begin("rayleigh-ritz", &si_rr);
       bdg_status st = rayleigh_ritz(U_[cur_], HU_[cur_], nu, nxb, m_, om);
+      sec_end(se_rr);
       if (st) return st;
       const int mm = (int)om.size();
       if (mm == 0) return fail(plan_, BDG_ERR_BREAKDOWN, "no positive Ritz values");
@@ -717,6 +757,8 @@ class Solver {
       // rows; the new Ritz block is then X-part + P, which spares the [D P]
       // columns a second pass
       bool haveP = nxb > 0 && nu > nxb;
+      int si_ex;
+      cudaEvent_t se_ex = sec_begin("extraction", &si_ex);
       if (haveP) {
         const int p0 = nxb / 2, pp = pu - p0;
         const double* Pd = Pc + (size_t)nxb * ldc;
@@ -745,6 +787,7 @@ class Solver {
           if ((st = update_dev(gpart(HU_[cur_], 0, pu), Qc, ldc, 0.0, gptr(HU_[nxt], 0), mmp))) return st;
         }
       }
+      sec_end(se_ex);
       if (dbg_ && haveP && !exact_images_)
         fprintf(stderr, "[bdg]   dbg P images after extraction %.3e\n", dbg_img(Pb_, HPb_, mmp));
       cur_ = nxt;
@@ -753,7 +796,7 @@ class Solver {
       if (exact_images_) {
         // images of the new Ritz block by the product itself: every residual
         // and every projected matrix then holds to the rounding of one product
-        if ((st = apply_fg(X, HX, mmp))) return st;
+        { int si_; cudaEvent_t se_ = sec_begin("apply ritz block", &si_); st = apply_fg(X, HX, mmp); sec_end(se_); if (st) return st; }
         refreshed_at = it;
       }
       // The images HX are carried by linear combination; their rounding
@@ -769,6 +812,8 @@ class Solver {
       }
       refresh_next = false;
       if (dbg_) fprintf(stderr, "[bdg]   dbg ritz X_f^T X_g - I %.3e\n", dbg_bi(X, mmp, mm, X, mmp, mm, true));
+      int si_res;
+      cudaEvent_t se_res = sec_begin("residuals", &si_res);
       // residuals R_f = HF - G w, R_g = HG - F w
       BDG_CUDA_TRY(plan_, cudaMemcpyAsync(Rb_, HX, sizeof(T) * vlen_ * mmp, cudaMemcpyDeviceToDevice, s_));
       HostMat Dw(2 * mmp, 2 * mmp);
@@ -795,6 +840,7 @@ class Solver {
         if ((st = update(Zb, cn, 1.0, side == 0 ? fptr(Rb_, 0) : gptr(Rb_, 0), mmp))) return st;
       }
       if (dbg_) fprintf(stderr, "[bdg]   dbg after null fix X_f^T X_g - I %.3e\n", dbg_bi(X, mmp, mm, X, mmp, mm, true));
+      sec_end(se_res);
       // residual norms
       std::vector<double> nr, nx;
       if ((st = colnorms(Rb_, mmp, nr))) return st;
@@ -874,12 +920,12 @@ class Solver {
       HostMat Sel(2 * mmp, 2 * nap);
       for (int jj = 0; jj < na; ++jj) Sel(act[jj], jj) = 1.0;
       if ((st = update_full(Rb_, mmp, Sel, Wb_, nap))) return st;
-      if ((st = directions(Wb_, nap))) return st;
-      if ((st = deflate(Wb_, 0, nap))) return st;
+      { int si_; cudaEvent_t se_ = sec_begin("inner directions", &si_); st = directions(Wb_, nap); sec_end(se_); if (st) return st; }
+      { int si_; cudaEvent_t se_ = sec_begin("deflate D", &si_); st = deflate(Wb_, 0, nap); sec_end(se_); if (st) return st; }
       // unit f- and g-parts before the product: the two real columns sharing
       // a complex vector then have equal norms, so the rounding crosstalk
       // between them in the FFTs stays at eps relative to each column
-      if ((st = normalize_parts(Wb_, nullptr, nap))) return st;
+      { int si_; cudaEvent_t se_ = sec_begin("normalize D", &si_); st = normalize_parts(Wb_, nullptr, nap); sec_end(se_); if (st) return st; }
       if (!exact_images_ && (st = apply_fg(Wb_, HWb_, nap))) return st;
       int nw = 2 * nap;
       if (haveP) {
@@ -909,20 +955,21 @@ class Solver {
       if (nw > 2 * nap) {
         T* WP = Wb_ + (long long)nap * vlen_;
         T* HWP = HWx ? HWx + (long long)nap * vlen_ : nullptr;
-        if ((st = cgs2(X, HX, mmp, WP, HWP, nap))) return st;
-        if ((st = biortho_block(WP, HWP, nap, 2 * nap, fptr(X, mmp), HWP ? fptr(HX, mmp) : nullptr, rtol_, &rp)))
-          return st;
+        { int si_; cudaEvent_t se_ = sec_begin("cgs2 P", &si_); st = cgs2(X, HX, mmp, WP, HWP, nap); sec_end(se_); if (st) return st; }
+        { int si_; cudaEvent_t se_ = sec_begin("biortho P", &si_);
+          st = biortho_block(WP, HWP, nap, 2 * nap, fptr(X, mmp), HWP ? fptr(HX, mmp) : nullptr, rtol_, &rp);
+          sec_end(se_); if (st) return st; }
       }
       const int rpp = (rp + 1) / 2;
-      if ((st = cgs2(X, HX, mmp + rpp, Wb_, HWx, nap))) return st;
+      { int si_; cudaEvent_t se_ = sec_begin("cgs2 D", &si_); st = cgs2(X, HX, mmp + rpp, Wb_, HWx, nap); sec_end(se_); if (st) return st; }
       int rd = 0;
-      if ((st = biortho_block(Wb_, HWx, nap, 2 * nap, fptr(X, mmp + rpp), HWx ? fptr(HX, mmp + rpp) : nullptr,
-                              rtol_, &rd)))
-        return st;
+      { int si_; cudaEvent_t se_ = sec_begin("biortho D", &si_);
+        st = biortho_block(Wb_, HWx, nap, 2 * nap, fptr(X, mmp + rpp), HWx ? fptr(HX, mmp + rpp) : nullptr, rtol_, &rd);
+        sec_end(se_); if (st) return st; }
       if (log_) fprintf(stderr, "[bdg]   block ranks P %d D %d\n", rp, rd);
       if (rp + rd == 0) return fail(plan_, BDG_ERR_BREAKDOWN, "search directions lost rank");
       // images of the new basis columns [P', D'] by one product
-      if (exact_images_ && (st = apply_fg(fptr(X, mmp), fptr(HX, mmp), rpp + (rd + 1) / 2))) return st;
+      if (exact_images_) { int si_; cudaEvent_t se_ = sec_begin("apply new columns", &si_); st = apply_fg(fptr(X, mmp), fptr(HX, mmp), rpp + (rd + 1) / 2); sec_end(se_); if (st) return st; }
       nxb = 2 * mmp;
       nu = 2 * (mmp + rpp) + rd;
     }
@@ -1001,10 +1048,7 @@ class Solver {
     double* d = dvec_ + 6 * big_;
     bdg_status st = colnorm_dev(bank, vlen_, pairs, d);
     if (st) return st;
-    out.assign(2 * pairs, 0.0);
-    BDG_CUDA_TRY(plan_, cudaMemcpyAsync(out.data(), d, sizeof(double) * 2 * pairs, cudaMemcpyDeviceToHost, s_));
-    BDG_CUDA_TRY(plan_, cudaStreamSynchronize(s_));
-    return BDG_OK;
+    return download(d, out, 2 * pairs);
   }
 
   bdg_status alloc(void** p, size_t bytes) {
@@ -1017,6 +1061,12 @@ class Solver {
     return BDG_OK;
   }
   void release() {
+    sec_report();
+    if (pinned_) {
+      cudaStreamSynchronize(s_);
+      cudaFreeHost(pinned_);
+      pinned_ = nullptr;
+    }
     for (void* p : owned_) cudaFree(p);
     owned_.clear();
   }
@@ -1040,6 +1090,9 @@ class Solver {
   double* dvec_ = nullptr;
   double* dws_ = nullptr;
   double* cnpart_ = nullptr;
+  static constexpr size_t PIN_DOUBLES = 1 << 20;   // 8 MB of pinned staging
+  double* pinned_ = nullptr;
+  size_t pin_off_ = 0;
   int big_ = 0;
   bool dbg_eigh_ = getenv("BDG_CHECK_EIGH") != nullptr;
   T* dbg_buf_ = nullptr;
@@ -1063,6 +1116,45 @@ class Solver {
   int fp32_stall_ = getenv("BDG_FP32_STALL") ? atoi(getenv("BDG_FP32_STALL")) : 1;
   bool log_ = getenv("BDG_LOG") != nullptr;
   std::vector<double> omega_, resid_;
+
+  // diagnostics (BDG_PROFILE): device time per solver section, from CUDA
+  // events on the solver's stream, printed when the solver is released
+  bool prof_ = getenv("BDG_PROFILE") != nullptr;
+  struct Section { std::string name; std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev; };
+  std::vector<Section> sections_;
+  cudaEvent_t sec_begin(const char* name, int* idx) {
+    if (!prof_) return nullptr;
+    int i = 0;
+    while (i < (int)sections_.size() && sections_[i].name != name) ++i;
+    if (i == (int)sections_.size()) sections_.push_back(Section{name, {}});
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s_);
+    sections_[i].ev.push_back({a, b});
+    *idx = i;
+    return b;
+  }
+  void sec_end(cudaEvent_t b) {
+    if (b) cudaEventRecord(b, s_);
+  }
+  void sec_report() {
+    if (!prof_ || sections_.empty()) return;
+    cudaStreamSynchronize(s_);
+    for (auto& sc : sections_) {
+      double ms = 0.0;
+      for (auto& pr : sc.ev) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, pr.first, pr.second);
+        ms += t;
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+      }
+      fprintf(stderr, "[bdg] prof %-3d-bit %-22s %5zu x %9.3f ms\n", (int)sizeof(R) * 8, sc.name.c_str(),
+              sc.ev.size(), ms);
+    }
+    sections_.clear();
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -1149,25 +1241,41 @@ bdg_status bdg_solve(bdg_plan_t plan, int k, int m, const void* X0, double* omeg
   // 256^2 workload (FP64 inner products cost about twenty FP32 ones)
   const char* env_inner = getenv("BDG_INNER_STEPS");
   S64.inner_steps_ = env_inner ? atoi(env_inner) : (S64.inner_fp32_ ? 12 : 8);
+  const bool log_phases = getenv("BDG_LOG") != nullptr;
+  auto mark = [&](const char* what) {
+    if (log_phases)
+      fprintf(stderr, "[bdg] %8.3f ms  %s\n",
+              1e3 * std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(), what);
+  };
   if (plan->prm.prec == BDG_MIXED) {
     Solver<float> S32(plan, s, m);
     S32.sigma_ = sigma;
     S32.rtol_ = 1e-4;
     S32.inner_steps_ = env_inner ? atoi(env_inner) : 12;
     if ((st = S32.init_buffers())) return st;
+    mark("FP32 buffers");
     if ((st = S32.start_random(X0, plan->prm.seed))) return st;
+    mark("FP32 start block");
     const double floor32 = getenv("BDG_FP32_FLOOR") ? atof(getenv("BDG_FP32_FLOOR")) : 3e-4;
     if ((st = S32.iterate(k, tol, maxit, floor32, &it1, &conv))) return st;
+    mark("FP32 phase");
     if ((st = S64.init_buffers())) return st;
+    mark("FP64 buffers");
     if ((st = transfer(S32, S64, s))) return st;
+    mark("transfer");
   } else {
     if ((st = S64.init_buffers())) return st;
+    mark("FP64 buffers");
     if ((st = S64.start_random(X0, plan->prm.seed))) return st;
+    mark("FP64 start block");
   }
+  mark("FP32 solver released");
   st = S64.iterate(k, tol, std::max(1, maxit - it1), 0.0, &it2, &conv);
   if (st) return st;
+  mark("FP64 phase");
   std::vector<double> res(k, INFINITY);
   if ((st = finish<double>(S64, k, omega, UV, res.data(), s))) return st;
+  mark("finish");
   int nc = 0;
   while (nc < k && nc < S64.mm_ && res[nc] <= tol) nc++;
   *nconv = nc;
