@@ -102,21 +102,25 @@ def gpe_rhs_componentwise(psi: np.ndarray, V: np.ndarray, w, beta_n: float,
     return np.stack([r1, r0, rm])
 
 
-ZERO_COMPONENT = 1e-24
+ZERO_COMPONENT = 1e-20
 
 
 def chemical_potentials(phi: np.ndarray, Hphi: np.ndarray) -> np.ndarray:
     """mu_j = <phi_j, (H Phi)_j> / ||phi_j||^2 (eq. chem-formula), with the
     relation mu_1 + mu_-1 = 2 mu_0 filling components that vanish
-    (||phi_j||^2 < 1e-24 on the unweighted grid sum; reading P3)."""
+    (||phi_j||^2 < 1e-20 ||Phi||^2 on unweighted grid sums; reading P3).  A
+    component that small is the decayed remnant of a ground-state iteration;
+    its own Rayleigh quotient is the energy of its slowest mode, not a
+    Lagrange multiplier of the stationary state."""
     phi = phi.reshape(3, -1)
     Hphi = Hphi.reshape(3, -1)
     nrm = np.sum(np.abs(phi) ** 2, axis=1)
+    small = nrm < ZERO_COMPONENT * np.sum(nrm)
     mu = np.full(3, np.nan)
     for j in range(3):
-        if nrm[j] >= ZERO_COMPONENT:
+        if not small[j]:
             mu[j] = np.real(np.vdot(phi[j], Hphi[j])) / nrm[j]
-    z1, z0, zm = (nrm < ZERO_COMPONENT)
+    z1, z0, zm = small
     if z0 and not z1 and not zm:
         mu[1] = 0.5 * (mu[0] + mu[2])
     elif z1 and zm and not z0:

@@ -200,7 +200,10 @@ static unsigned blocks_for(long long n) {
 // Chemical potentials by eq. chem-formula: with mu = 0, the FG product of
 // (0, Phi) gives (H_- Phi) = H Phi; mu_j = <phi_j, (H Phi)_j> / |phi_j|^2,
 // and the relation mu_1 + mu_-1 = 2 mu_0 fills components with
-// |phi_j|^2 < 1e-24 (unweighted grid sum).
+// |phi_j|^2 < 1e-20 |Phi|^2 (unweighted grid sums): a component that small
+// is the decayed remnant of the ground-state iteration, and its own Rayleigh
+// quotient (the energy of its slowest mode) would shift the whole m = j
+// branch of the operator.
 static bdg_status compute_mu(bdg_plan_t plan, cudaStream_t s, double* mu) {
   const long long np = plan->grid.npts;
   bdg_status st = ensure(plan, SLOT_VEC_A, sizeof(double2) * 6 * np);
@@ -221,7 +224,7 @@ static bdg_status compute_mu(bdg_plan_t plan, cudaStream_t s, double* mu) {
     st = dot_cols<double>(plan, x + (3 + j) * np, x + (3 + j) * np, np, &den[j], s);
     if (st) return st;
   }
-  const double tiny = 1e-24;
+  const double tiny = 1e-20 * (den[0] + den[1] + den[2]);
   bool z[3];
   for (int j = 0; j < 3; ++j) {
     z[j] = den[j] < tiny;

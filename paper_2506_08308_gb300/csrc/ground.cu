@@ -13,6 +13,11 @@
 // Hessian of the Lagrangian (eqs. def_A + def_B at a real Phi), then
 // Phi <- P_SM(Phi + d).  A Newton step that does not lower the residual
 // hands back to 50 flow steps.
+// Newton converges to any stationary point.  A converged state is therefore
+// tested for negative curvature of the energy on S_M along the directions
+// that move population between spin components; a saddle (e.g. the
+// antiferromagnetic state when q > 0 makes the polar state lower) is left
+// along that direction and the flow resumes (at most three times).
 //
 // P_SM scales the components, phi_j <- sigma_j phi_j, to mass 1 and
 // magnetization M with sigma_1 sigma_-1 = sigma_0^2 (closed form).  The
@@ -178,6 +183,27 @@ __global__ void k_gs_resid(const double2* __restrict__ hphi, const double2* __re
 }
 
 // S_z Phi
+// Directions that move population between the spin components of Phi = (a,
+// b, c): kind 0: (0, (a + c) / sqrt2, 0) (from +-1 into 0), kind 1:
+// (b, 0, b) / sqrt2 and kind 2: (b, 0, -b) / sqrt2 (from 0 into +-1).  At a
+// stationary state that is not a minimum (e.g. the antiferromagnetic state
+// (a, 0, a) when q > 0 makes the polar state lower) one of them has negative
+// curvature.
+__global__ void k_gs_transfer(const double2* __restrict__ phi, long long np, int kind, double2* __restrict__ out) {
+  const double h = 0.70710678118654752440;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < np;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double a = phi[i].x, b = phi[np + i].x, c = phi[2 * np + i].x;
+    double o0 = 0.0, o1 = 0.0, o2 = 0.0;
+    if (kind == 0) o1 = h * (a + c);
+    else if (kind == 1) { o0 = h * b; o2 = h * b; }
+    else { o0 = h * b; o2 = -h * b; }
+    out[i] = make_double2(o0, 0.0);
+    out[np + i] = make_double2(o1, 0.0);
+    out[2 * np + i] = make_double2(o2, 0.0);
+  }
+}
+
 __global__ void k_gs_sz(const double2* __restrict__ phi, long long np, double2* __restrict__ out) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < 3 * np;
        e += (long long)gridDim.x * blockDim.x) {
@@ -230,9 +256,28 @@ class GroundState {
     double alpha = 0.0;
     if ((st = stab(phi_, &alpha))) return st;
     double c = 1.0 / tau + alpha;
-    int phase = 1, flow_left = 0;
+    int phase = 1, flow_left = 0, restarts = 0, flow_only = 0;
     double last = INFINITY;
-    while (it < maxit && *res > tol) {
+    while (it < maxit) {
+      if (*res <= tol) {
+        // a converged stationary state that is a saddle of the energy on S_M
+        // is left along its negative-curvature direction and the flow resumes
+        bool unstable = false;
+        if (restarts >= 3) break;
+        if ((st = stability(&unstable))) return st;
+        if (!unstable) break;
+        ++restarts;
+        const double nphi = std::sqrt(dot1(phi_, phi_, &st));
+        if (st) return st;
+        k_gs_axpby<<<nblk(n3_), 256, 0, s_>>>(n3_, 1e-2 * nphi, cp_, 1.0, phi_);
+        BDG_CUDA_TRY(plan_, cudaGetLastError());
+        if ((st = project(phi_)) || (st = residual(phi_, res, mu))) return st;
+        phase = 1;
+        flow_left = 0;
+        flow_only = 500;   // no Newton step until the unstable component has grown
+        last = INFINITY;
+        continue;
+      }
       if (phase == 1 || flow_left > 0) {
         if ((st = flow_step(c))) return st;
         flow_left = flow_left > 0 ? flow_left - 1 : 0;
@@ -241,11 +286,15 @@ class GroundState {
         if (it % 50 == 0) {
           if ((st = stab(phi_, &alpha))) return st;
           c = 1.0 / tau + alpha;
-          if (phase == 1 && *res > 0.99 * last) phase = 2;
+          if (phase == 1 && flow_only == 0 && *res > 0.99 * last) phase = 2;
           last = *res;
         }
         const double mmax = std::max(std::fabs(mu[0]), std::max(std::fabs(mu[1]), std::fabs(mu[2])));
-        if (phase == 1 && *res < newton_start * (1.0 + mmax)) phase = 2;
+        if (flow_only > 0) {
+          --flow_only;
+          phase = 1;
+        }
+        if (phase == 1 && flow_only == 0 && *res < newton_start * (1.0 + mmax)) phase = 2;
       } else {
         int products = 0;
         if ((st = newton_step(c, &products))) return st;
@@ -357,8 +406,9 @@ class GroundState {
     double v[6];
     if ((st = dots(d, np_, v))) return st;
     bool z[3];
+    const double tiny = 1e-20 * (v[3] + v[4] + v[5]);   // vanishing components, relative to |Phi|^2
     for (int j = 0; j < 3; ++j) {
-      z[j] = v[3 + j] < 1e-24;
+      z[j] = v[3 + j] < tiny;
       mu[j] = z[j] ? NAN : v[j] / v[3 + j];
     }
     if (z[1] && !z[0] && !z[2]) mu[1] = 0.5 * (mu[0] + mu[2]);
@@ -444,11 +494,10 @@ class GroundState {
     return v;
   }
 
-  // one inexact Newton step from phi_ into trial_; *products = H_+ products
-  bdg_status newton_step(double c, int* products) {
-    const double eta = 1e-2;
-    const int maxcg = 500;
-    *products = 0;
+  // Multipliers m3 = mu + lambda S_z of the least-squares fit H Phi ~
+  // (mu + lambda S_z) Phi at phi_ and the weighted-orthonormal basis z_ of
+  // span{Phi, S_z Phi} (the normal directions of S_M); hphi_ = H Phi.
+  bdg_status tangent_setup(double m3[3]) {
     bdg_status st = hphi(phi_);
     if (st) return st;
     // multipliers: least squares of H Phi ~ (mu + lambda S_z) Phi
@@ -472,7 +521,9 @@ class GroundState {
       mu = (g[3] * g[2] - g[1] * g[4]) / det;
       lam = (g[0] * g[4] - g[1] * g[3]) / det;
     }
-    const double m3[3] = {mu + lam, mu, mu - lam};
+    m3[0] = mu + lam;
+    m3[1] = mu;
+    m3[2] = mu - lam;
     // weighted-orthonormal basis of span{Phi, S_z Phi}
     nz_ = 0;
     {
@@ -492,6 +543,51 @@ class GroundState {
         nz_ = 2;
       }
     }
+    return BDG_OK;
+  }
+
+  // Stability of a converged stationary state: the curvature
+  // <d, P H_+ P d> / <d, d> of the energy on S_M along the population-transfer
+  // directions (k_gs_transfer).  *unstable is set, and the unit direction of
+  // most negative curvature left in cp_, when a curvature is below
+  // -1e-9 (1 + max |mu|).
+  bdg_status stability(bool* unstable) {
+    *unstable = false;
+    double m3[3];
+    bdg_status st = tangent_setup(m3);
+    if (st) return st;
+    const double mmax = std::max(std::fabs(m3[0]), std::max(std::fabs(m3[1]), std::fabs(m3[2])));
+    const double nphi = dot1(phi_, phi_, &st);
+    if (st) return st;
+    double best = -1e-9 * (1.0 + mmax);
+    for (int kind = 0; kind < 3; ++kind) {
+      k_gs_transfer<<<nblk(np_), 256, 0, s_>>>(phi_, np_, kind, cz_);
+      BDG_CUDA_TRY(plan_, cudaGetLastError());
+      if ((st = tangent(cz_))) return st;
+      const double dd = dot1(cz_, cz_, &st);
+      if (st) return st;
+      if (!(dd > 1e-16 * nphi)) continue;
+      if ((st = hplus(cz_, cap_, m3)) || (st = tangent(cap_))) return st;
+      const double kappa = dot1(cz_, cap_, &st) / dd;
+      if (st) return st;
+      if (kappa < best) {
+        best = kappa;
+        *unstable = true;
+        k_gs_axpby<<<nblk(n3_), 256, 0, s_>>>(n3_, 1.0 / std::sqrt(dd), cz_, 0.0, cp_);
+        BDG_CUDA_TRY(plan_, cudaGetLastError());
+      }
+    }
+    return BDG_OK;
+  }
+
+  // one inexact Newton step from phi_ into trial_; *products = H_+ products
+  bdg_status newton_step(double c, int* products) {
+    const double eta = 1e-2;
+    const int maxcg = 500;
+    *products = 0;
+    double m3[3];
+    bdg_status st = tangent_setup(m3);
+    if (st) return st;
     // b = -P r, r = H Phi - (mu + lambda S_z) Phi;  CG on P H_+ P x = b
     k_gs_resid<<<nblk(n3_), 256, 0, s_>>>(hphi_, phi_, np_, m3[0], m3[1], m3[2], cr_);
     BDG_CUDA_TRY(plan_, cudaGetLastError());

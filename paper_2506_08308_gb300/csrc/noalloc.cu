@@ -125,10 +125,11 @@ extern "C" bdg_status bdg_chemical_potentials_noalloc(bdg_plan_t plan, double* m
       (which ? den : num)[j] = h[0] + h[3];
     }
   }
-  // components with |phi_j|^2 < 1e-24 take their mu from mu_1 + mu_-1 = 2 mu_0
+  // components with |phi_j|^2 < 1e-20 |Phi|^2 take their mu from mu_1 + mu_-1 = 2 mu_0
   bool z[3];
+  const double tiny = 1e-20 * (den[0] + den[1] + den[2]);
   for (int j = 0; j < 3; ++j) {
-    z[j] = den[j] < 1e-24;
+    z[j] = den[j] < tiny;
     mu[j] = z[j] ? NAN : num[j] / den[j];
   }
   if (z[1] && !z[0] && !z[2]) mu[1] = 0.5 * (mu[0] + mu[2]);

@@ -137,3 +137,27 @@ def test_non_interacting_oscillator_states():
     v = np.stack([psi1, 0 * psi1, psi1]).reshape(1, 3, -1)
     for y in (op.hplus(v), op.hminus(v)):
         assert relerr(y, g * v) < 1e-12
+
+
+def test_vanishing_component_rule_is_relative():
+    """Reading P3: a component counts as vanishing when ||phi_j||^2 <
+    1e-20 ||Phi||^2 (unweighted sums), and then takes mu_j from
+    mu_1 + mu_-1 = 2 mu_0.  The antiferromagnetic state (a, 0, a) with a
+    remnant phi_0 = 1e-12 a (relative norm^2 1e-24; an absolute threshold of
+    1e-24 would not catch it on a 64-point grid) gives mu_0 = (mu_1 + mu_-1)/2
+    exactly, whatever the remnant's shape; a populated phi_0 = 1e-6 a keeps
+    its own Rayleigh quotient."""
+    w = W1
+    V = synth.potential(w)
+    x = synth.axes(w)[0]
+    a = np.exp(-0.5 * x ** 2)
+    for eps, vanishing in ((1e-12, True), (1e-6, False)):
+        phi = np.stack([a, eps * a * (1.0 + x), a])
+        H = spin1.hamiltonian(phi, V, w, w.beta_n, w.beta_s, w.p, w.q)
+        mu = spin1.chemical_potentials(phi, H)
+        own0 = np.dot(phi[1], H[1]) / np.dot(phi[1], phi[1])
+        if vanishing:
+            assert np.sum(phi[1] ** 2) > 1e-24 and abs(mu[1] - 0.5 * (mu[0] + mu[2])) < 1e-12
+            assert abs(own0 - mu[1]) > 1e-3
+        else:
+            assert abs(mu[1] - own0) < 1e-12 * abs(own0)
