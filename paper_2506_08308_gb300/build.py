@@ -41,7 +41,7 @@ def _compile(src: str, hdr_time: float, verbose: bool) -> str:
     obj = os.path.join(BUILD, os.path.splitext(os.path.basename(src))[0] + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_time):
         return obj
-    cmd = [nvcc()] + ARCH + FLAGS + ["-c", src, "-o", obj]
+    cmd = [nvcc()] + ARCH + FLAGS + os.environ.get("BDG_NVCC_EXTRA", "").split() + ["-c", src, "-o", obj]
     if verbose:
         print(" ".join(cmd), flush=True)
     res = subprocess.run(cmd, capture_output=True, text=True)
