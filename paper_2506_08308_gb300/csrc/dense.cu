@@ -55,7 +55,7 @@ __global__ void k_dgemm(bool ta, bool tb, int m, int n, int k, double alpha, con
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_jacobi(int n, const double* __restrict__ Ag, int lda,
                                                  double* __restrict__ w, double* __restrict__ Vg,
-                                                 int max_sweeps) {
+                                                 int max_sweeps, float off_tol) {
   extern __shared__ float sm[];
   const int ld = n + 1;
   float* A = sm;                 // [n][ld]
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(int n, const double* __restrict
       red[32] = st;
     }
     __syncthreads();
-    const bool done = red[0] <= 1e-12f * red[32];
+    const bool done = red[0] <= off_tol * red[32];
     __syncthreads();
     if (done) break;
     for (int r = 0; r < np2 - 1; ++r) {
@@ -529,7 +529,9 @@ cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double
     cudaEventCreate(&pj[1]);
     cudaEventRecord(pj[0], s);
   }
-  k_jacobi<<<1, 1024, sm, s>>>(n, A, lda, w, V, 30);
+  // converged to off(A) <= 1e-12 |A|^2: the FP64 refinement needs a start
+  // this close (a stop at 1e-7 left backward errors up to 5e-2)
+  k_jacobi<<<1, 1024, sm, s>>>(n, A, lda, w, V, 30, 1e-12f);
   if ((e = cudaGetLastError())) return e;
   if (prof) {
     cudaEventRecord(pj[1], s);
@@ -624,6 +626,122 @@ cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Rank-revealing pivoted Cholesky (see dense.cuh), one CTA of 1024 threads:
+// right-looking, the lower triangle of the working matrix S in shared
+// memory; step k pivots the largest remaining diagonal to position k, forms
+// column k of L and updates the trailing lower triangle.  The inverse of L1
+// comes from row-wise forward substitution, X_i = (e_i - sum_{j<i} L_ij X_j)
+// / L_ii.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_pchol(int n, const double* __restrict__ A, int lda, double tol,
+                                                double* __restrict__ L, double* __restrict__ M, int ldo,
+                                                int* __restrict__ rank_dev) {
+  extern __shared__ double psm[];
+  double* S = psm;                           // [n][n]
+  double* dinv = S + (size_t)n * n;          // [n]: 1 / L_ii
+  int* perm = reinterpret_cast<int*>(dinv + n);
+  __shared__ double sh_d0;
+  __shared__ int sh_p, sh_r;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, j = e - i * n;
+    S[e] = A[(long long)i * lda + j];
+  }
+  for (int i = tid; i < n; i += nt) perm[i] = i;
+  if (tid == 0) sh_r = n;
+  __syncthreads();
+  if (tid < 32) {
+    double m = 0.0;
+    for (int i = tid; i < n; i += 32) m = fmax(m, S[i * n + i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (tid == 0) sh_d0 = m;
+  }
+  __syncthreads();
+  const double dmin = tol * sh_d0;
+  for (int k = 0; k < n; ++k) {
+    if (tid < 32) {   // pivot: largest remaining diagonal (first index on ties)
+      double m = -1.0;
+      int p = k;
+      for (int i = k + tid; i < n; i += 32) {
+        const double d = S[i * n + i];
+        if (d > m) { m = d; p = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double m2 = __shfl_xor_sync(0xffffffffu, m, o);
+        const int p2 = __shfl_xor_sync(0xffffffffu, p, o);
+        if (m2 > m || (m2 == m && p2 < p)) { m = m2; p = p2; }
+      }
+      if (tid == 0) {
+        sh_p = p;
+        if (!(m > dmin) || !(sh_d0 > 0.0)) sh_r = k;
+      }
+    }
+    __syncthreads();
+    if (sh_r == k) break;
+    const int p = sh_p;
+    if (p != k) {   // symmetric swap of rows / columns k and p (full matrix)
+      for (int j = tid; j < n; j += nt) {
+        const double t = S[k * n + j];
+        S[k * n + j] = S[p * n + j];
+        S[p * n + j] = t;
+      }
+      __syncthreads();
+      for (int i = tid; i < n; i += nt) {
+        const double t = S[i * n + k];
+        S[i * n + k] = S[i * n + p];
+        S[i * n + p] = t;
+      }
+      if (tid == 0) {
+        const int t = perm[k];
+        perm[k] = perm[p];
+        perm[p] = t;
+      }
+      __syncthreads();
+    }
+    const double lkk = sqrt(S[k * n + k]);
+    __syncthreads();
+    for (int i = k + 1 + tid; i < n; i += nt) S[i * n + k] /= lkk;
+    if (tid == 0) S[k * n + k] = lkk;
+    __syncthreads();
+    // trailing update of the lower triangle and its mirror (rows and columns
+    // of later pivots are read in full by the swaps above)
+    const int m = n - k - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = k + 1 + e / m, j = k + 1 + e % m;
+      S[i * n + j] -= S[i * n + k] * S[j * n + k];
+    }
+    __syncthreads();
+  }
+  const int r = sh_r;
+  // L in the original row order: row perm[i] of L is row i of the factor
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, c = e - i * n;
+    L[(long long)perm[i] * ldo + c] = (c < r && c <= i) ? S[i * n + c] : 0.0;
+    M[(long long)i * ldo + c] = 0.0;
+  }
+  __syncthreads();
+  // X = L1^-1 (r x r, lower), row by row: X_ii = 1 / L_ii in dinv, X_ic
+  // (c < i) in the strictly upper triangle of S at S[c * n + i] (free once
+  // the factor was copied out; L1 stays in the lower triangle)
+  for (int i = tid; i < r; i += nt) dinv[i] = 1.0 / S[i * n + i];
+  __syncthreads();
+  for (int i = 1; i < r; ++i) {
+    for (int c = tid; c < i; c += nt) {
+      double acc = -S[i * n + c] * dinv[c];
+      for (int j = c + 1; j < i; ++j) acc -= S[i * n + j] * S[c * n + j];
+      S[c * n + i] = acc * dinv[i];
+    }
+    __syncthreads();
+  }
+  // M = P^T [L1^-T; 0]: row perm[i] (i < r) holds (L1^-T)_{i c} = X_{c i}
+  for (int e = tid; e < r * r; e += nt) {
+    const int i = e / r, c = e - i * r;
+    M[(long long)perm[i] * ldo + c] = c == i ? dinv[i] : (c > i ? S[i * n + c] : 0.0);
+  }
+  if (tid == 0) *rank_dev = r;
+}
+
 // X = I, lam = diag(A): the start for nearly diagonal matrices
 __global__ void k_identity_start(int n, const double* __restrict__ A, int lda, double* __restrict__ X,
                                  double* __restrict__ lam) {
@@ -632,6 +750,16 @@ __global__ void k_identity_start(int n, const double* __restrict__ A, int lda, d
     X[e] = i == j ? 1.0 : 0.0;
     if (i == j) lam[i] = A[(long long)i * lda + i];
   }
+}
+
+cudaError_t pchol(int n, const double* A, int lda, double tol, double* L, double* M, int ldo, int* rank_dev,
+                  cudaStream_t s) {
+  if (n <= 0 || n > SMALL_MAX || ldo < n) return cudaErrorInvalidValue;
+  const size_t sm = sizeof(double) * ((size_t)n * n + n) + sizeof(int) * (size_t)n;
+  cudaError_t e = cudaFuncSetAttribute(k_pchol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_pchol<<<1, 1024, sm, s>>>(n, A, lda, tol, L, M, ldo, rank_dev);
+  return cudaGetLastError();
 }
 
 cudaError_t eigh(int n, const double* A, int lda, double* w, double* V, double* ws, int refine_steps,

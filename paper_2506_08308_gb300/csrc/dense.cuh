@@ -29,6 +29,17 @@ size_t eigh_workspace_doubles(int n);
 cudaError_t eigh(int n, const double* A, int lda, double* w, double* V, double* ws, int refine_steps,
                  cudaStream_t s, double floor_rel = 0.0, bool from_identity = false);
 
+// Rank-revealing Cholesky factorization with symmetric pivoting of a
+// symmetric positive semidefinite n x n FP64 matrix A (row-major, lda):
+// P A P^T = [L1; L2] [L1; L2]^T, pivoting on the largest remaining
+// diagonal and stopping at the first pivot <= tol * max_i A_ii.  Writes, in
+// the original row order and with leading dimension ldo (>= n, columns
+// r .. n-1 zero): L = P^T [L1; L2] (A ~ L L^T) and M = P^T [L1^-T; 0]
+// (L^T M = I_r); the rank r goes to *rank_dev (device).  One CTA, the
+// matrix staged in shared memory (n <= SMALL_MAX).
+cudaError_t pchol(int n, const double* A, int lda, double tol, double* L, double* M, int ldo, int* rank_dev,
+                  cudaStream_t s);
+
 // Elementwise helpers on small matrices (row-major).
 // B[i][j] = A[i][j] * dl[i] * dr[j]  (dl / dr may be NULL = ones)
 cudaError_t dscale_small(int m, int n, const double* A, int lda, const double* dl, const double* dr,

@@ -271,6 +271,8 @@ class Solver {
     if (alloc(&p, sizeof(double) * 2 * CN_BLOCKS * (size_t)cap_))
       return fail(plan_, BDG_ERR_NOMEM, "column-norm workspace allocation failed");
     cnpart_ = (double*)p;
+    if (alloc(&p, 256)) return fail(plan_, BDG_ERR_NOMEM, "solver workspace allocation failed");
+    dint_ = (int*)p;
     if (cudaMallocHost((void**)&pinned_, sizeof(double) * PIN_DOUBLES) != cudaSuccess) {
       cudaGetLastError();
       pinned_ = nullptr;
@@ -582,28 +584,57 @@ class Solver {
       Kt = Ks;
       ldt = n;
     }
-    std::vector<double> lam;
-    // stage 2 (scale == false) re-solves matrices that are diagonal up to
-    // the rounding of stage 1: the refinement starts from the identity
-    bdg_status st = eigh_dev(n, Kt, ldt, dvec_, Q, lam, 1e-11, !scale);   // lam <= 1e-10 lam_max is cut
-    if (st) return st;
-    const double lmax = lam[n - 1];
-    if (!(lmax > 0)) return fail(plan_, BDG_ERR_BREAKDOWN, "projected H_+ is not positive");
-    int i0 = 0;
-    while (i0 < n && !(lam[i0] > 1e-10 * lmax)) ++i0;
-    const int r = n - i0;
-    std::vector<double> sl(r), isl(r);
-    for (int a = 0; a < r; ++a) {
-      sl[a] = std::sqrt(lam[i0 + a]);
-      isl[a] = 1.0 / sl[a];
+    // Factor K_+ = Lh Lh^T on its numerical range with a right inverse Minv
+    // (Lh^T Minv = I): stage 1 by the rank-revealing pivoted Cholesky of the
+    // unit-diagonal Kt (pivots <= 1e-10 of the largest are cut), stage 2
+    // (scale == false, a Kt diagonal up to the rounding of stage 1) by its
+    // eigen-decomposition refined from the identity,
+    // Kt = Q diag(lam) Q^T, lam <= 1e-10 lam_max cut.
+    double* Lh = dmat_[MAT_B];    // n x r
+    double* Minv = dmat_[MAT_M];  // n x r
+    bdg_status st = BDG_OK;
+    int r = 0;
+    if (scale && pchol_) {
+      double* Lc = dmat_[MAT_A];
+      double* Mc = dmat_[MAT_E];
+      { int si_; cudaEvent_t se_ = sec_begin("  pivoted Cholesky", &si_);
+        st = cuda(pchol(n, Kt, ldt, 1e-10, Lc, Mc, n, dint_, s_), "pchol");
+        sec_end(se_); if (st) return st; }
+      std::vector<double> rr;
+      int rk = 0;
+      BDG_CUDA_TRY(plan_, cudaMemcpyAsync(&rk, dint_, sizeof(int), cudaMemcpyDeviceToHost, s_));
+      if ((st = sync_stream())) return st;
+      r = rk;
+      if (r <= 0) return fail(plan_, BDG_ERR_BREAKDOWN, "projected H_+ is not positive");
+      if ((st = cuda(dscale_small(n, r, Lc, n, dsq, nullptr, Lh, r, s_), "scale")) ||
+          (st = cuda(dscale_small(n, r, Mc, n, dinv, nullptr, Minv, r, s_), "scale")))
+        return st;
+    } else {
+      std::vector<double> lam;
+      // stage 2 re-solves matrices that are diagonal up to the rounding of
+      // stage 1: the refinement starts from the identity
+      st = eigh_dev(n, Kt, ldt, dvec_, Q, lam, 1e-11, !scale);   // lam <= 1e-10 lam_max is cut
+      if (st) return st;
+      const double lmax = lam[n - 1];
+      if (!(lmax > 0)) return fail(plan_, BDG_ERR_BREAKDOWN, "projected H_+ is not positive");
+      int i0 = 0;
+      while (i0 < n && !(lam[i0] > 1e-10 * lmax)) ++i0;
+      r = n - i0;
+      std::vector<double> sl(r), isl(r);
+      for (int a = 0; a < r; ++a) {
+        sl[a] = std::sqrt(lam[i0 + a]);
+        isl[a] = 1.0 / sl[a];
+      }
+      double* dsl = dvec_ + big_;
+      double* disl = dsl + big_;
+      if ((st = upload(dsl, sl)) || (st = upload(disl, isl))) return st;
+      // Lh = D^1/2 Q_r diag(sqrt(lam)), Minv = D^-1/2 Q_r diag(1/sqrt(lam))
+      if ((st = cuda(dscale_small(n, r, Q + i0, n, dsq, dsl, Lh, r, s_), "scale")) ||
+          (st = cuda(dscale_small(n, r, Q + i0, n, dinv, disl, Minv, r, s_), "scale")))
+        return st;
     }
-    double* dsl = dvec_ + big_;
-    double* disl = dsl + big_;
-    if ((st = upload(dsl, sl)) || (st = upload(disl, isl))) return st;
-    double* Lh = dmat_[MAT_B];   // n x r: D^1/2 Q_r diag(sqrt(lam))
     double* KL = dmat_[MAT_C];   // n x r
     double* C = dmat_[MAT_D];    // r x r
-    if ((st = cuda(dscale_small(n, r, Q + i0, n, dsq, dsl, Lh, r, s_), "scale"))) return st;
     if ((st = cuda(dgemm_small(false, false, n, r, n, 1.0, Km, ldm, Lh, r, 0.0, KL, r, s_), "gemm"))) return st;
     if ((st = cuda(dgemm_small(true, false, r, r, n, 1.0, Lh, r, KL, r, 0.0, C, r, s_), "gemm"))) return st;
     if ((st = cuda(dsym_small(r, C, r, s_), "sym"))) return st;
@@ -627,17 +658,15 @@ class Solver {
         (st = cuda(dzero_small(zrows, ldc, Qc, ldc, s_), "zero")))
       return st;
     if (mm == 0) return BDG_OK;
-    double* dsw = disl + big_;
+    double* dsw = dvec_ + 3 * big_;
     double* disw = dsw + big_;
     if ((st = upload(dsw, sw)) || (st = upload(disw, isw))) return st;
-    double* QS = dmat_[MAT_B];   // L^-T = D^-1/2 Q_r diag(1/sqrt(lam)), then L
     double* ZS = dmat_[MAT_C];   // Z_sel diag(sqrt(w)) then diag(1/sqrt(w))
-    if ((st = cuda(dscale_small(n, r, Q + i0, n, dinv, disl, QS, r, s_), "scale"))) return st;
+    // Pc = Minv Z_sel W^1/2, Qc = Lh Z_sel W^-1/2
     if ((st = cuda(dscale_small(r, mm, Z + j0, r, nullptr, dsw, ZS, mm, s_), "scale"))) return st;
-    if ((st = cuda(dgemm_small(false, false, n, mm, r, 1.0, QS, r, ZS, mm, 0.0, Pc, ldc, s_), "gemm"))) return st;
-    if ((st = cuda(dscale_small(n, r, Q + i0, n, dsq, dsl, QS, r, s_), "scale"))) return st;
+    if ((st = cuda(dgemm_small(false, false, n, mm, r, 1.0, Minv, r, ZS, mm, 0.0, Pc, ldc, s_), "gemm"))) return st;
     if ((st = cuda(dscale_small(r, mm, Z + j0, r, nullptr, disw, ZS, mm, s_), "scale"))) return st;
-    if ((st = cuda(dgemm_small(false, false, n, mm, r, 1.0, QS, r, ZS, mm, 0.0, Qc, ldc, s_), "gemm"))) return st;
+    if ((st = cuda(dgemm_small(false, false, n, mm, r, 1.0, Lh, r, ZS, mm, 0.0, Qc, ldc, s_), "gemm"))) return st;
     return BDG_OK;
   }
 
@@ -675,8 +704,10 @@ class Solver {
     double* Kp = dmat_[MAT_G1];
     double* Km = dmat_[MAT_G2];
     { int si_; cudaEvent_t se_ = sec_begin("  RR grams", &si_);
-      st = gram(fpart(U, 0, pu), fpart(HU, 0, pu), Kp);
-      if (!st) st = gram(gpart(U, 0, pu), gpart(HU, 0, pu), Km);
+      // K_+ = U^T H_+ U and K_- = V^T H_- V are symmetric: the tiles on and
+      // above the diagonal are formed, the rest mirrored
+      st = gram(fpart(U, 0, pu), fpart(HU, 0, pu), Kp, true);
+      if (!st) st = gram(gpart(U, 0, pu), gpart(HU, 0, pu), Km, true);
       sec_end(se_); if (st) return st; }
     if ((st = cuda(dsym_small(nu, Kp, ldg, s_), "sym")) || (st = cuda(dsym_small(nu, Km, ldg, s_), "sym")))
       return st;
@@ -981,7 +1012,7 @@ class Solver {
   bdg_status cgs2(const T* Bk, const T* HBk, int bp, T* W, T* HW, int wp) {
     bdg_status st = BDG_OK;
     const int nw = 2 * wp;
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < cgs_passes_; ++pass) {
       double* c1 = dmat_[MAT_G1];
       double* c2 = dmat_[MAT_G2];
       if ((st = gram(gpart(Bk, 0, bp), fpart(W, 0, wp), c1))) return st;
@@ -1085,11 +1116,15 @@ class Solver {
   size_t gws_bytes_ = 0;
   double* dsm_ = nullptr;
   enum { MAT_G1, MAT_G2, MAT_A, MAT_B, MAT_C, MAT_D, MAT_E, MAT_P, MAT_Q, MAT_HOST, MAT_P1, MAT_Q1,
-         MAT_P2, MAT_Q2, MAT_T, MAT_K2P, MAT_K2M, NMAT };
+         MAT_P2, MAT_Q2, MAT_T, MAT_K2P, MAT_K2M, MAT_M, NMAT };
   double* dmat_[NMAT] = {};
   double* dvec_ = nullptr;
   double* dws_ = nullptr;
   double* cnpart_ = nullptr;
+  int* dint_ = nullptr;
+  // stage 1 of the Rayleigh-Ritz step factors K_+ by pivoted Cholesky
+  // (otherwise by its eigen-decomposition)
+  bool pchol_ = getenv("BDG_RR_EIGH") == nullptr;
   static constexpr size_t PIN_DOUBLES = 1 << 20;   // 8 MB of pinned staging
   double* pinned_ = nullptr;
   size_t pin_off_ = 0;
@@ -1107,6 +1142,7 @@ class Solver {
   InnerPCG<double> in64_;
   double rtol_ = 1e-10;
   double zero_tol2_ = 1e-12;
+  int cgs_passes_ = getenv("BDG_CGS_PASSES") ? atoi(getenv("BDG_CGS_PASSES")) : 2;
   // images H X of the Ritz block and of new basis columns by the product
   // itself (otherwise carried by linear combination, refreshed every 20
   // iterations; carried images drift by eps |coefficients| and stall strong
