@@ -124,27 +124,34 @@ __global__ void __launch_bounds__(1024) k_jacobi(int n, const double* __restrict
       __syncthreads();
       // A <- J^T A J and V <- V J in one pass: a work item is the 2 x 2 block
       // (row pair k, column pair l) of A -- rows first, then columns, as the
-      // two one-sided updates would do -- or a row of V's column pair l.  A
-      // dummy pair (odd n) has p == q and c = 1, s = 0, which makes its
-      // duplicate reads and writes agree.
-      const int nblk = npair * npair;
-      for (int e = tid; e < nblk + npair * n; e += nt) {
-        if (e < nblk) {
-          const int k = e / npair, l = e - k * npair;
-          const int p = pq[2 * k], q = pq[2 * k + 1], u = pq[2 * l], v = pq[2 * l + 1];
-          const float ck = cs[2 * k], sk = cs[2 * k + 1], cl = cs[2 * l], sl = cs[2 * l + 1];
-          const float x00 = A[p * ld + u], x01 = A[p * ld + v], x10 = A[q * ld + u], x11 = A[q * ld + v];
+      // two one-sided updates would do -- or the rows of V's column pair l.
+      // Warps take row pairs (or V's column pairs), lanes column pairs (or
+      // rows): no index division, and the row pair's indices and rotation
+      // are broadcast loads.  A dummy pair (odd n) has p == q and c = 1,
+      // s = 0, which makes its duplicate reads and writes agree.
+      const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+      for (int k = warp; k < npair; k += nwarp) {
+        const int p = pq[2 * k], q = pq[2 * k + 1];
+        const float ck = cs[2 * k], sk = cs[2 * k + 1];
+        float* Ap = A + p * ld;
+        float* Aq = A + q * ld;
+        for (int l = lane; l < npair; l += 32) {
+          const int u = pq[2 * l], v = pq[2 * l + 1];
+          const float cl = cs[2 * l], sl = cs[2 * l + 1];
+          const float x00 = Ap[u], x01 = Ap[v], x10 = Aq[u], x11 = Aq[v];
           const float r00 = ck * x00 - sk * x10, r01 = ck * x01 - sk * x11;
           const float r10 = sk * x00 + ck * x10, r11 = sk * x01 + ck * x11;
-          A[p * ld + u] = cl * r00 - sl * r01;
-          A[p * ld + v] = sl * r00 + cl * r01;
-          A[q * ld + u] = cl * r10 - sl * r11;
-          A[q * ld + v] = sl * r10 + cl * r11;
-        } else {
-          const int f = e - nblk, l = f / n, i = f - l * n;
-          const int u = pq[2 * l], v = pq[2 * l + 1];
-          if (u == v) continue;
-          const float cl = cs[2 * l], sl = cs[2 * l + 1];
+          Ap[u] = cl * r00 - sl * r01;
+          Ap[v] = sl * r00 + cl * r01;
+          Aq[u] = cl * r10 - sl * r11;
+          Aq[v] = sl * r10 + cl * r11;
+        }
+      }
+      for (int l = warp; l < npair; l += nwarp) {
+        const int u = pq[2 * l], v = pq[2 * l + 1];
+        if (u == v) continue;
+        const float cl = cs[2 * l], sl = cs[2 * l + 1];
+        for (int i = lane; i < n; i += 32) {
           const float vp = V[i * ld + u], vq = V[i * ld + v];
           V[i * ld + u] = cl * vp - sl * vq;
           V[i * ld + v] = sl * vp + cl * vq;
@@ -551,8 +558,8 @@ cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double
   if (!(amax > 0)) return cudaSuccess;
   if (depth == 0) floor *= amax;   // the caller's floor is relative at the top level
   const double tau = 1e-4 * amax;
-  // at the top level the runs of at most RC_NS_MAX columns are resolved by one
-  // launch (FP64 Jacobi per run); wider runs, and deeper levels, re-solve in turn
+  // runs of at most RC_NS_MAX columns are resolved by one launch (FP64
+  // Jacobi per run); wider runs re-solve in turn on their projection
   ClusterList cl;
   cl.count = 0;
   int ns_max = 0;
@@ -569,7 +576,7 @@ cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double
     // runs whose eigenvalues all lie below the caller's floor (|lambda| of the
     // original matrix) are not needed resolved: the caller discards them
     const double top = std::max(std::fabs(hw[i0] + shift), std::fabs(hw[i1 - 1] + shift));
-    if (ns >= 2 && spread > 0 && !degenerate && !(top < floor) && depth == 0 && ns <= RC_NS_MAX &&
+    if (ns >= 2 && spread > 0 && !degenerate && !(top < floor) && ns <= RC_NS_MAX &&
         cl.count < RC_MAX_CLUSTERS) {
       cl.start[cl.count] = i0;
       cl.size[cl.count] = ns;
@@ -615,6 +622,8 @@ cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double
     }
     i0 = i1;
   }
+  if (prof && depth == 0)
+    fprintf(stderr, "[bdg]   clusters n %d: %d batched (widest %d)\n", n, cl.count, ns_max);
   if (cl.count > 0) {
     const size_t smr = resolve_smem_bytes(n, ns_max);
     if ((e = cudaFuncSetAttribute(k_resolve_clusters, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr))) return e;
