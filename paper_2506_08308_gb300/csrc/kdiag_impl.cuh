@@ -66,8 +66,10 @@ __global__ void __launch_bounds__(256) k_kd_contig(const typename CT<R>::T* x,
 #pragma unroll
       for (int k2 = 0; k2 < N1; ++k2) {
         const int kk = kidx<N>(t + N1 * s + N2 * k2);
-        const double d = c.shift + c.scale * c.kappa[axis] * (double)(kk * kk);
-        b[s][k2] = b[s][k2] * (R)(c.norm / d);
+        // the symbol in the arithmetic precision R (FP64 division runs at a
+        // small fraction of the FP32 rate on this part)
+        const R d = (R)c.shift + (R)(c.scale * c.kappa[axis]) * (R)(kk * kk);
+        b[s][k2] = b[s][k2] * ((R)c.norm / d);
       }
   }
   if (mode == KD_FWD) {
@@ -139,13 +141,15 @@ __global__ void __launch_bounds__(W * Split<N>::N1) k_kd_strided(const typename 
       const int k1 = i1 < c.n[1] / 2 ? i1 : i1 - c.n[1];
       extra = c.kappa[1] * (double)(k1 * k1);
     }
+    // the symbol in the arithmetic precision R, per-thread constants hoisted
+    const R base_d = (R)(c.shift + c.scale * extra), sk0 = (R)(c.scale * c.kappa[0]);
 #pragma unroll
     for (int s = 0; s < L::S; ++s)
 #pragma unroll
       for (int k2 = 0; k2 < N1; ++k2) {
         const int kk = kidx<N>(j + N1 * s + N2 * k2);
-        const double d = c.shift + c.scale * (c.kappa[0] * (double)(kk * kk) + extra);
-        b[s][k2] = b[s][k2] * (R)(c.norm / d);
+        const R d = base_d + sk0 * (R)(kk * kk);
+        b[s][k2] = b[s][k2] * ((R)c.norm / d);
       }
   }
   if (mode == KD_FWD) {
