@@ -405,15 +405,17 @@ def run_density_only(args):
 
 
 def run_profile_solve(args):
-    """A few FP64 solver iterations of the workload on an operator built from
-    the normalised seeded start spinor (no ground state, so that a profiler
-    sees few launches before the solver's); prints the time per iteration."""
+    """A few mixed-precision solver iterations of the workload (the FP32
+    phase, then FP64 iterations with FP32 inner solves) on an operator built
+    from the normalised seeded start spinor (no ground state, so that a
+    profiler sees few launches before the solver's); prints the time per
+    iteration."""
     import torch
     from paper_2506_08308_gb300 import bdg
     w = W
     phi = synth.initial_spinor(w)
     phi = phi / np.sqrt(np.prod(w.h) * np.sum(phi ** 2))
-    plan = bdg.Plan(bdg.params_from(w, mu=(5.7, 5.7, 5.7), prec=bdg.FP64, tol=TOL, maxit=args.profile_solve),
+    plan = bdg.Plan(bdg.params_from(w, mu=(5.7, 5.7, 5.7), prec=bdg.MIXED, tol=TOL, maxit=args.profile_solve),
                     synth.potential(w), phi.reshape(-1))
     X0 = torch.from_numpy(synth.random_block(w, w.m, complex_=True)).cuda()
     t0 = time.perf_counter()
@@ -623,7 +625,8 @@ def run_ours(args):
     if not args.skip_launch_count:
         try:
             from torch.profiler import ProfilerActivity, profile
-            with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            # (CUDA activity alone records no kernels with the torch build of the GPU machine)
+            with profile(activities=[ProfilerActivity.CPU, ProfilerActivity.CUDA]) as prof:
                 step()
                 torch.cuda.synchronize()
             per_kernel = {}
@@ -645,8 +648,8 @@ def run_ours(args):
                 shares = {"step_device_ms": total / 1000.0, "launches_per_step": n,
                           "kernels": [{"name": k, "launches": c, "ms": t / 1000.0, "share": t / total}
                                       for k, (c, t) in top]}
-        except Exception:  # noqa: BLE001 -- auxiliary evidence only
-            launches, shares = None, None
+        except Exception as exc:  # noqa: BLE001 -- auxiliary evidence only
+            launches, shares = None, {"error": f"{type(exc).__name__}: {exc}"[:300]}
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_iters > 0:
