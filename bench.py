@@ -174,10 +174,13 @@ APPLY_SOURCES = ["paper_2506_08308_gb300/csrc/apply_impl.cuh", "paper_2506_08308
                  "paper_2506_08308_gb300/csrc/apply_f32.cu", "paper_2506_08308_gb300/csrc/common.cuh"]
 
 
-def apply_traffic():
-    """DRAM bytes per call of the FP32 block product from the committed ncu
-    summary (its TRAFFIC line), or None when the kernels changed since the
-    counters were taken."""
+def apply_traffic(w=None):
+    """DRAM bytes per call of the FP32 block product on the 256^2 workload
+    (m = 48) from the committed ncu summary (its TRAFFIC line); None for
+    another workload or when the kernels changed since the counters were
+    taken."""
+    if w is not None and (w.n != W.n or w.m != W.m):
+        return None
     path = os.path.join(ROOT, "profiles", "bdg_apply_c64_2d_n256.md")
     try:
         with open(path) as f:
@@ -484,7 +487,8 @@ def run_batched(args):
             "ground states from bdg_ground_state)",
             "config": {"workload": "batched_2d_x64", "instances": len(ws), "grids": {f"{n}^2": c for n, c in grids.items()},
                        "k": ks[0], "m": ms_[0], "precision": "mixed FP32/FP64", "tol": TOL,
-                       "call": "one bdg_solve_batched per step (problems back to back on one stream)"},
+                       "call": ("one bdg_solve_batched per step (a work queue over the instances, largest first, "
+                                "served by up to 8 host threads with a stream each)")},
             "converged_pairs": conv, "requested_pairs": sum(ks) * args.steps,
             "fp64_solver": {"value": conv64 / (ms64 / 1000.0), "unit": UNIT, "converged": conv64, "of": sum(ks),
                             "seconds": ms64 / 1000.0},
@@ -602,7 +606,7 @@ def run_ours(args):
     alg_bytes = (96 * w.m + 16) * w.npts          # x in + y out (c64, 6 fields) + (Phi, V) FP32 table
     achieved = alg_bytes / t_apply / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": apply_traffic(),
+                "frac": achieved / peaks["hbm_gbs"], "traffic": apply_traffic(w),
                 "kernel": f"bdg_apply FG c64, m={w.m} block, {'x'.join(map(str, w.n))} grid (all line passes)",
                 "us_per_call": t_apply * 1e6, "algorithmic_bytes_per_call": alg_bytes,
                 "peak_kind": peak_kind + " burst copy"}

@@ -129,6 +129,32 @@ bdg_status bdg_biortho(bdg_plan_t plan, int dtype, void* F, void* G, int ncol, c
                        const void* Gl, int nlock, int* rank, void* stream);
 
 /*
+ * bdg_gram -- the Gram matrix of two blocks of complex columns taken as
+ * real columns (real part, imaginary part): G = A^T B, the contraction of
+ * the bi-orthogonal Gram-Schmidt (S = F^H G, Theorem "Biorthogonality") and
+ * of the projected matrices U^H H_+ U, V^H H_- V of the Rayleigh-Ritz step
+ * (Section 3.2).
+ *   A, B    device, ncol_a (ncol_b) complex columns of n elements, column
+ *           stride lda (ldb) elements, interleaved complex of dtype.
+ *   G       device, double[2 ncol_a][2 ncol_b] row-major:
+ *           G[2i+s][2j+t] = sum_{r<n} part_s(A_i[r]) part_t(B_j[r]),
+ *           part_0 the real and part_1 the imaginary part.
+ *   engine  BDG_GRAM_SIMT: FP32 (C64) or double-float with about 1e-15 of
+ *           sum |a b| (C128) on the CUDA cores, row chunks summed in FP64;
+ *           BDG_GRAM_TENSOR: every element split into three BF16 slices,
+ *           the six leading slice products accumulated in FP32 by the
+ *           tensor cores (tcgen05), row chunks summed in FP64: FP32 accuracy
+ *           (about 1e-6 of sum |a b|) for either dtype; needs 2 ncol_b <= 160
+ *           (BDG_ERR_UNSUPPORTED beyond).
+ * Sums are taken in a fixed order (repeated calls give identical G).  The
+ * workspace is allocated and freed in stream order on `stream`.
+ * ncol_a or ncol_b == 0 is a no-op; n == 0 gives G = 0.
+ */
+typedef enum { BDG_GRAM_SIMT = 0, BDG_GRAM_TENSOR = 1 } bdg_gram_engine;
+bdg_status bdg_gram(int dtype, int engine, const void* A, long long lda, int ncol_a, const void* B, long long ldb,
+                    int ncol_b, long long n, double* G, void* stream);
+
+/*
  * bdg_solve -- the k smallest positive excitation energies and their
  * Bogoliubov amplitudes (Sections 3.1-3.2; solver details are this library's
  * own, see the design notes).
@@ -156,12 +182,18 @@ bdg_status bdg_solve(bdg_plan_t plan, int k, int m, const void* X0, double* omeg
 /*
  * bdg_solve_batched -- the k[i] smallest positive excitations of count
  * independent problems (the batched workload: many parameter sets and grids,
- * eqs. lrep-d and constrain for each), solved back to back on one stream.
- * Each entry behaves as bdg_solve(plans[i], k[i], m[i], NULL, omega[i],
- * UV ? UV[i] : NULL, resid ? resid[i] : NULL, &nconv[i], stream) with the
- * plan's seeded start block.  Every plan is attempted; the first failing
- * status is returned (bdg_last_error(NULL) names the plan), and nconv[i] is
- * filled for all entries.
+ * eqs. lrep-d and constrain for each).  Each entry behaves as
+ * bdg_solve(plans[i], k[i], m[i], NULL, omega[i], UV ? UV[i] : NULL,
+ * resid ? resid[i] : NULL, &nconv[i], s) with the plan's seeded start
+ * block.  The instances form a work queue (largest grids first) served by
+ * up to 8 host threads (environment BDG_BATCH_WORKERS), each solving on a
+ * stream of its own that starts after the work queued on `stream`; with a
+ * grid above 2^20 points the instances are solved one at a time on
+ * `stream`.  The plans must be distinct (BDG_ERR_INVALID otherwise) and on
+ * the current device.  Every plan is attempted; the first failing status
+ * (in plan order) is returned (bdg_last_error(NULL) names the plan), and
+ * nconv[i] is filled for all entries.  Returns after every output is
+ * written.
  */
 bdg_status bdg_solve_batched(bdg_plan_t* plans, int count, const int* k, const int* m, double** omega,
                              void** UV, double** resid, int* nconv, void* stream);

@@ -19,6 +19,9 @@ Contents
                        when it lies in null(H_+) (Section 2.3; reading P7).
   solve_iterative      block structure-preserving subspace iteration (reading P8).
   residuals, normalize_fg, fg_to_uv.
+  pair_gram            S = F^T G over real columns (real, imaginary part) of two blocks
+                       of complex columns: the Gram of the bi-orthogonal Gram-Schmidt
+                       (Theorem "Biorthogonality") and of the projected matrices.
 
 The inner products here are the unweighted Euclidean ones; the weight h^d
 enters only the normalization <f, g> = 1/4 of eq. constrainfg (reading P11).
@@ -188,6 +191,18 @@ def deflation_bases(op, phi, par_tol=1e-12, null_tol=1e-8):
 # --------------------------------------------------------------------------
 # residuals and the iterative solver
 # --------------------------------------------------------------------------
+def pair_gram(A, B):
+    """Gram matrix of real columns: A (P, n) and B (Q, n) complex rows are
+    taken as 2P and 2Q real vectors (real part, imaginary part), and
+    S[2i+s, 2j+t] = sum_r part_s(A[i, r]) part_t(B[j, r]) in FP64, together
+    with S_abs, the same sums of absolute products (the scale of its
+    rounding).  This is the inner product of the bi-orthogonality relations
+    (Theorem "Biorthogonality") on packed real vectors."""
+    Ar = np.stack([A.real, A.imag], axis=1).reshape(2 * A.shape[0], -1).astype(np.float64)
+    Br = np.stack([B.real, B.imag], axis=1).reshape(2 * B.shape[0], -1).astype(np.float64)
+    return Ar @ Br.T, np.abs(Ar) @ np.abs(Br).T
+
+
 def residuals(op, F, G, om):
     """r_i = sqrt(|H_+ f - w g|^2 + |H_- g - w f|^2) / (w sqrt(|f|^2 + |g|^2)),
     which equals |M x - w x| / (|w| |x|) for x = (u, v) (reading P9).

@@ -22,6 +22,7 @@ OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_BREAKDOWN, ERR_NOT_CONVERGED, ERR_TIME
 FP64, MIXED = 0, 1
 C128, C64 = 0, 1
 UV, FG = 0, 1
+GRAM_SIMT, GRAM_TENSOR = 0, 1
 
 STATUS_NAMES = {0: "BDG_OK", 1: "BDG_ERR_INVALID", 2: "BDG_ERR_NOMEM", 3: "BDG_ERR_CUDA",
                 4: "BDG_ERR_BREAKDOWN", 5: "BDG_ERR_NOT_CONVERGED", 6: "BDG_ERR_TIMEOUT",
@@ -30,7 +31,7 @@ STATUS_NAMES = {0: "BDG_OK", 1: "BDG_ERR_INVALID", 2: "BDG_ERR_NOMEM", 3: "BDG_E
 # every symbol include/bdg.h declares
 EXPORTS = ("bdg_plan_create", "bdg_plan_destroy", "bdg_plan_mu", "bdg_apply", "bdg_biortho",
            "bdg_solve", "bdg_solve_batched", "bdg_get_solve_stats", "bdg_ground_state",
-           "bdg_chemical_potentials_noalloc", "bdg_perturbed_density",
+           "bdg_chemical_potentials_noalloc", "bdg_perturbed_density", "bdg_gram",
            "bdg_last_error")
 
 
@@ -82,6 +83,8 @@ def load() -> ctypes.CDLL:
     lib.bdg_chemical_potentials_noalloc.argtypes = [vp, dp, vp]
     lib.bdg_perturbed_density.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, dp, dp, ctypes.c_int,
                                           ctypes.c_double, vp, vp]
+    lib.bdg_gram.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_longlong, ctypes.c_int, vp,
+                             ctypes.c_longlong, ctypes.c_int, ctypes.c_longlong, vp, vp]
     lib.bdg_last_error.argtypes = [vp]
     lib.bdg_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -284,6 +287,32 @@ class Plan:
         s = SolveStats()
         _check(self.lib, self.lib.bdg_get_solve_stats(self.handle, ctypes.byref(s)), self.handle)
         return {f: getattr(s, f) for f, _ in SolveStats._fields_}
+
+
+def gram(A, B, engine: int = GRAM_TENSOR, out=None, stream=None):
+    """bdg_gram: G = A^T B over real columns of two blocks of complex columns
+    (torch complex64 or complex128 tensors of shape (ncol, n), contiguous
+    rows, same dtype and device); G has shape (2 ncol_a, 2 ncol_b), FP64."""
+    import torch
+    lib = load()
+    if A.dtype != B.dtype or A.dtype not in (torch.complex64, torch.complex128):
+        raise ValueError("A and B must both be complex64 or both complex128")
+    if A.dim() != 2 or B.dim() != 2 or A.shape[1] != B.shape[1]:
+        raise ValueError("A and B must be (ncol, n) with the same n")
+    if A.device != B.device or A.device.type != "cuda":
+        raise ValueError("A and B must be CUDA tensors on one device")
+    if A.stride(1) != 1 or B.stride(1) != 1:
+        raise ValueError("rows of A and B must be contiguous")
+    shape = (2 * A.shape[0], 2 * B.shape[0])
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float64, device=A.device)
+    else:
+        _check_out(out, shape, torch.float64, A.device)
+    dtype = C64 if A.dtype == torch.complex64 else C128
+    st = lib.bdg_gram(dtype, int(engine), _ptr(A), A.stride(0), A.shape[0], _ptr(B), B.stride(0), B.shape[0],
+                      A.shape[1], _ptr(out), _stream_handle(stream))
+    _check(lib, st)
+    return out
 
 
 def solve_batched(plans, ks, ms, want_vectors: bool = True, stream=None, allow_not_converged: bool = False):

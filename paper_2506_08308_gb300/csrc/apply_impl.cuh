@@ -278,7 +278,7 @@ static cudaError_t launch_row(const ApplyArgs<R>& g, cudaStream_t s) {
   constexpr int N1 = Split<N>::N1, RR = 32 / N1;
   const size_t sm = sizeof(T) * (size_t)N * (1 + 2 * 6 * RR);
   auto kern = k_row<N, R>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = allow_dynamic_smem((const void*)kern, sm);
   if (e != cudaSuccess) return e;
   const int nlast = g.grid->n[g.grid->dim - 1];
   const long long rows_per_vec = g.grid->npts / nlast;
@@ -296,7 +296,7 @@ static cudaError_t launch_axis_w(const ApplyArgs<R>& g, int ax, long long st, cu
   constexpr int N1 = Split<N>::N1;
   const size_t sm = sizeof(T) * ((size_t)N + (size_t)W * (N + 1));
   auto kern = k_axis<N, R, W>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = allow_dynamic_smem((const void*)kern, sm);
   if (e != cudaSuccess) return e;
   const long long tiles = g.grid->npts / ((long long)N * W);
   const long long blocks = tiles * 6 * g.nvec;

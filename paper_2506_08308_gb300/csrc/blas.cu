@@ -192,24 +192,48 @@ inline int tile_mult(int n) {
 
 // G = sum over chunks; with tile > 0, entries below the diagonal tiles are
 // read from their mirror (upper-triangle Grams)
-__global__ void k_gram_reduce_upper(const double* __restrict__ part, int nchunks, int P2, int Q2, int tile,
-                                    double* __restrict__ G) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= P2 * Q2) return;
-  const int i = e / Q2, j = e - i * Q2;
-  const int src = (i / tile > j / tile) ? j * Q2 + i : e;
+// in a fixed order: thread (x, y) of a 32 x 8 block sums chunks y, y + 8,
+// ... of one output (independent loads in flight), then the eight sums are
+// added in order of y
+__global__ void __launch_bounds__(256) k_gram_reduce_upper(const double* __restrict__ part, int nchunks, int P2,
+                                                           int Q2, int tile, double* __restrict__ G) {
+  __shared__ double t[8][33];
+  const int x = threadIdx.x & 31, y = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + x, nout = P2 * Q2;
   double s = 0.0;
-  for (int c = 0; c < nchunks; ++c) s += part[(long long)c * P2 * Q2 + src];
-  G[e] = s;
+  if (e < nout) {
+    const int i = e / Q2, j = e - i * Q2;
+    const int src = (i / tile > j / tile) ? j * Q2 + i : e;
+#pragma unroll 4
+    for (int c = y; c < nchunks; c += 8) s += part[(long long)c * nout + src];
+  }
+  t[y][x] = s;
+  __syncthreads();
+  if (y == 0 && e < nout) {
+    double g = t[0][x];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) g += t[q][x];
+    G[e] = g;
+  }
 }
 
-__global__ void k_gram_reduce(const double* __restrict__ part, int nchunks, int nout,
-                              double* __restrict__ G) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nout) return;
+__global__ void __launch_bounds__(256) k_gram_reduce(const double* __restrict__ part, int nchunks, int nout,
+                                                     double* __restrict__ G) {
+  __shared__ double t[8][33];
+  const int x = threadIdx.x & 31, y = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + x;
   double s = 0.0;
-  for (int c = 0; c < nchunks; ++c) s += part[(long long)c * nout + i];
-  G[i] = s;
+  if (e < nout)
+#pragma unroll 4
+    for (int c = y; c < nchunks; c += 8) s += part[(long long)c * nout + e];
+  t[y][x] = s;
+  __syncthreads();
+  if (y == 0 && e < nout) {
+    double g = t[0][x];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) g += t[q][x];
+    G[e] = g;
+  }
 }
 
 // One thread per row, 16 real output columns (8 pairs) per CTA column group.
@@ -383,7 +407,7 @@ cudaError_t gram_pairs(const PairBlock<R>& A, const PairBlock<R>& B, double* G_d
     cudaError_t e8 = cudaGetLastError();
     if (e8 != cudaSuccess) return e8;
     const int nout8 = P2 * Q2;
-    k_gram_reduce_upper<<<(nout8 + 255) / 256, 256, 0, s>>>((const double*)ws, (int)nch, P2, Q2,
+    k_gram_reduce_upper<<<(nout8 + 31) / 32, 256, 0, s>>>((const double*)ws, (int)nch, P2, Q2,
                                                             up ? 16 * mp : (1 << 30), G_dev);
     return cudaGetLastError();
   }
@@ -391,7 +415,7 @@ cudaError_t gram_pairs(const PairBlock<R>& A, const PairBlock<R>& B, double* G_d
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nout = P2 * Q2;
-  k_gram_reduce<<<(nout + 255) / 256, 256, 0, s>>>((const double*)ws, (int)nchunks, nout, G_dev);
+  k_gram_reduce<<<(nout + 31) / 32, 256, 0, s>>>((const double*)ws, (int)nchunks, nout, G_dev);
   return cudaGetLastError();
 }
 
@@ -407,12 +431,12 @@ cudaError_t update_pairs(const PairBlock<R>& A, const double* C_dev, int ldc, do
   dim3 grid((unsigned)((A.n + 255) / 256), (unsigned)((2 * Q + UCOLS - 1) / UCOLS));
   cudaError_t e;
   if (sizeof(R) == 8) {
-    e = cudaFuncSetAttribute(k_update_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = allow_dynamic_smem((const void*)k_update_df, sm);
     if (e != cudaSuccess) return e;
     k_update_df<<<grid, 256, sm, s>>>(*reinterpret_cast<const PairBlock<double>*>(&A), C_dev, ldc, beta,
                                       reinterpret_cast<double2*>(Y), ldy, Q, alpha);
   } else {
-    e = cudaFuncSetAttribute(k_update<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = allow_dynamic_smem((const void*)k_update<R>, sm);
     if (e != cudaSuccess) return e;
     k_update<R><<<grid, 256, sm, s>>>(A, C_dev, ldc, beta, Y, ldy, Q, alpha);
   }

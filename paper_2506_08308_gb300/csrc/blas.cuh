@@ -30,6 +30,14 @@ cudaError_t gram_pairs(const PairBlock<R>& A, const PairBlock<R>& B, double* G_d
                        size_t ws_bytes, cudaStream_t s, bool upper = false);
 size_t gram_workspace_bytes(int P, int Q, long long n);
 
+// The same Gram (full, no triangle) on the tensor cores with split-BF16
+// operands and FP32 accumulation: FP32 accuracy for FP32 or FP64 blocks.
+// Needs 2 B.cols <= 160; ws as for gram_pairs.
+bool gram_tc_supported(int P, int Q);
+template <typename R>
+cudaError_t gram_pairs_tc(const PairBlock<R>& A, const PairBlock<R>& B, double* G_dev, void* ws,
+                          size_t ws_bytes, cudaStream_t s);
+
 // Y[:, q].t = beta * Y[:, q].t + alpha * sum_{p,s} A[:, p].s * C[(2p+s) * ldc + 2q+t]
 // C is FP64 on the device (row-major 2P x 2Q with leading dimension ldc);
 // A and Y must not overlap.

@@ -3,6 +3,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -18,6 +20,20 @@ static thread_local std::string g_thread_error = "no error";
 
 void set_thread_error(const std::string& msg) { g_thread_error = msg; }
 const char* thread_error() { return g_thread_error.c_str(); }
+
+cudaError_t allow_dynamic_smem(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> granted;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& g = granted[{func, dev}];
+  if (bytes <= g) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) g = bytes;
+  return e;
+}
 
 bdg_status fail(bdg_plan_t plan, bdg_status st, const std::string& msg) {
   if (plan) plan->err = msg;
@@ -47,6 +63,9 @@ bdg_status ensure(bdg_plan_t plan, int slot, size_t bytes) {
     return fail(plan, BDG_ERR_NOMEM, "device allocation of " + std::to_string(want) + " bytes failed");
   }
   b.bytes = want;
+  // diagnostics (BDG_POISON): NaN bytes in new scratch, as for the solver's buffers
+  if (getenv("BDG_POISON") && cudaMemset(b.ptr, 0xFF, want) != cudaSuccess)
+    return fail(plan, BDG_ERR_CUDA, "scratch fill failed");
   return BDG_OK;
 }
 
@@ -526,6 +545,41 @@ bdg_status bdg_apply(bdg_plan_t plan, int mode, int dtype, const void* x, void* 
 const char* bdg_last_error(bdg_plan_t plan) {
   if (plan) return plan->err.empty() ? "no error" : plan->err.c_str();
   return thread_error();
+}
+
+bdg_status bdg_gram(int dtype, int engine, const void* A, long long lda, int ncol_a, const void* B, long long ldb,
+                    int ncol_b, long long n, double* G, void* stream) {
+  if (dtype != BDG_C64 && dtype != BDG_C128) return fail(nullptr, BDG_ERR_INVALID, "dtype must be BDG_C64 or BDG_C128");
+  if (engine != BDG_GRAM_SIMT && engine != BDG_GRAM_TENSOR)
+    return fail(nullptr, BDG_ERR_INVALID, "engine must be BDG_GRAM_SIMT or BDG_GRAM_TENSOR");
+  if (ncol_a < 0 || ncol_b < 0 || n < 0) return fail(nullptr, BDG_ERR_INVALID, "negative size");
+  if (ncol_a == 0 || ncol_b == 0) return BDG_OK;
+  if (!A || !B || !G) return fail(nullptr, BDG_ERR_INVALID, "A, B and G must be device pointers");
+  if ((ncol_a > 1 && lda < n) || (ncol_b > 1 && ldb < n))
+    return fail(nullptr, BDG_ERR_INVALID, "column stride below the column length");
+  if (engine == BDG_GRAM_TENSOR && !gram_tc_supported(ncol_a, ncol_b))
+    return fail(nullptr, BDG_ERR_UNSUPPORTED, "tensor-core Gram needs 2 ncol_b <= 160");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ws_bytes = gram_workspace_bytes(ncol_a, ncol_b, n > 0 ? n : 1);
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, ws_bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, BDG_ERR_NOMEM, "Gram workspace allocation failed");
+  }
+  cudaError_t e;
+  if (dtype == BDG_C128) {
+    PairBlock<double> a{(const double2*)A, lda, n, ncol_a}, b{(const double2*)B, ldb, n, ncol_b};
+    e = engine == BDG_GRAM_TENSOR ? gram_pairs_tc<double>(a, b, G, ws, ws_bytes, s)
+                                  : gram_pairs<double>(a, b, G, ws, ws_bytes, s, false);
+  } else {
+    PairBlock<float> a{(const float2*)A, lda, n, ncol_a}, b{(const float2*)B, ldb, n, ncol_b};
+    e = engine == BDG_GRAM_TENSOR ? gram_pairs_tc<float>(a, b, G, ws, ws_bytes, s)
+                                  : gram_pairs<float>(a, b, G, ws, ws_bytes, s, false);
+  }
+  const cudaError_t ef = cudaFreeAsync(ws, s);
+  if (e == cudaSuccess) e = ef;
+  if (e != cudaSuccess) return fail(nullptr, BDG_ERR_CUDA, std::string("bdg_gram: ") + cudaGetErrorString(e));
+  return BDG_OK;
 }
 
 bdg_status bdg_get_solve_stats(bdg_plan_t plan, bdg_solve_stats* st) {

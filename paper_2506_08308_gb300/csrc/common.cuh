@@ -47,6 +47,12 @@ BDG_COMPLEX_OPS(double2, double)
 void set_thread_error(const std::string& msg);
 const char* thread_error();
 
+// Raise the dynamic shared-memory limit of kernel `func` on the current
+// device to at least `bytes`.  The limit only grows: host threads that
+// launch the same kernel with different sizes (concurrent solves) never
+// lower it under one another.  Thread-safe.
+cudaError_t allow_dynamic_smem(const void* func, size_t bytes);
+
 #define BDG_CUDA_TRY(plan, call)                                                       \
   do {                                                                                 \
     cudaError_t e__ = (call);                                                          \

@@ -527,7 +527,7 @@ cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double
                               double floor, double shift, cudaStream_t s) {
   const size_t sm = sizeof(float) * (2 * (size_t)n * (n + 1) + 2 * (n / 2 + 1)) +
                     sizeof(int) * 2 * (n / 2 + 1) + sizeof(float) * 64;
-  cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = allow_dynamic_smem((const void*)k_jacobi, sm);
   if (e != cudaSuccess) return e;
   static const bool prof = getenv("BDG_PROFILE_EIGH") != nullptr;
   cudaEvent_t pj[2] = {};
@@ -626,7 +626,7 @@ cudaError_t jacobi_multilevel(int n, const double* A, int lda, double* w, double
     fprintf(stderr, "[bdg]   clusters n %d: %d batched (widest %d)\n", n, cl.count, ns_max);
   if (cl.count > 0) {
     const size_t smr = resolve_smem_bytes(n, ns_max);
-    if ((e = cudaFuncSetAttribute(k_resolve_clusters, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr))) return e;
+    if ((e = allow_dynamic_smem((const void*)k_resolve_clusters, smr))) return e;
     k_resolve_clusters<<<cl.count, 256, smr, s>>>(n, A, lda, w, V, cl);
     if ((e = cudaGetLastError())) return e;
   }
@@ -765,7 +765,7 @@ cudaError_t pchol(int n, const double* A, int lda, double tol, double* L, double
                   cudaStream_t s) {
   if (n <= 0 || n > SMALL_MAX || ldo < n) return cudaErrorInvalidValue;
   const size_t sm = sizeof(double) * ((size_t)n * n + n) + sizeof(int) * (size_t)n;
-  cudaError_t e = cudaFuncSetAttribute(k_pchol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = allow_dynamic_smem((const void*)k_pchol, sm);
   if (e != cudaSuccess) return e;
   k_pchol<<<1, 1024, sm, s>>>(n, A, lda, tol, L, M, ldo, rank_dev);
   return cudaGetLastError();

@@ -180,12 +180,15 @@ struct Line {
       for (int k2 = 0; k2 < N1; ++k2) ex[t + N1 * s + N2 * k2] = b[s][k2];
     sync();
   }
-  // natural order in ex -> spectral columns (for an inverse-only transform)
-  __device__ __forceinline__ static void fromNatural(T (&b)[S][N1], int t, const T* ex) {
+  // natural order in ex -> spectral columns (for an inverse-only transform).
+  // Ends with a barrier: the read pattern differs from the write pattern of
+  // invB, which follows, so every thread must finish reading first.
+  __device__ __forceinline__ static void fromNatural(T (&b)[S][N1], int t, const T* ex, Sync sync) {
 #pragma unroll
     for (int s = 0; s < S; ++s)
 #pragma unroll
       for (int k2 = 0; k2 < N1; ++k2) b[s][k2] = ex[t + N1 * s + N2 * k2];
+    sync();
   }
 };
 

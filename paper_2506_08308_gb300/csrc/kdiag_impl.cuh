@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) k_kd_contig(const typename CT<R>::T* x,
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) ex[t + N1 * n2] = a[n2];
     __syncwarp();
-    L::fromNatural(b, t, ex);
+    L::fromNatural(b, t, ex, WarpSync());
   } else {
     L::fwdA(a, t, ex, tw, WarpSync());
     L::fwdB(b, t, ex);
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(W * Split<N>::N1) k_kd_strided(const typename 
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) ex[j + N1 * n2] = a[n2];
     __syncthreads();
-    L::fromNatural(b, j, ex);
+    L::fromNatural(b, j, ex, BlockSync());
   } else {
     L::fwdA(a, j, ex, tw, BlockSync());
     L::fwdB(b, j, ex);
@@ -172,7 +172,7 @@ static cudaError_t kd_contig(const KdArgs<R>& g, const KdCoef& c, const typename
   constexpr int N1 = Split<N>::N1, LPC = 8 * (32 / N1);
   const size_t sm = sizeof(T) * ((size_t)N + (size_t)LPC * N);
   auto kern = k_kd_contig<N, R>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = allow_dynamic_smem((const void*)kern, sm);
   if (e != cudaSuccess) return e;
   const int ax = g.grid->dim - 1;
   const long long nlines = g.grid->npts / N * g.nplanes;
@@ -187,7 +187,7 @@ static cudaError_t kd_strided_w(const KdArgs<R>& g, const KdCoef& c, int ax, lon
   constexpr int N1 = Split<N>::N1;
   const size_t sm = sizeof(T) * ((size_t)N + (size_t)W * (N + 1));
   auto kern = k_kd_strided<N, R, W>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = allow_dynamic_smem((const void*)kern, sm);
   if (e != cudaSuccess) return e;
   const long long tiles = g.grid->npts / ((long long)N * W);
   kern<<<(unsigned)(tiles * g.nplanes), W * N1, sm, g.stream>>>(x, y, g.grid->npts, st, tiles, g.tw[ax],

@@ -25,12 +25,14 @@
 // FP32 floor, then continues in FP64 from the FP32 Ritz vectors.  All
 // projected problems are solved in FP64 accuracy (dense.cuh).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "apply.cuh"
@@ -309,7 +311,18 @@ class Solver {
 
   // ---- primitive wrappers ----------------------------------------------
   // G (2P x 2Q) of real columns, FP64 on device
-  bdg_status gram(const PairBlock<R>& A, const PairBlock<R>& B, double* G, bool upper = false) {
+  // Grams for which FP32 accuracy suffices -- every Gram of the FP32 phase,
+  // and the first pass of the two-pass Gram-Schmidt, whose second pass
+  // (double-float) removes what the first leaves -- run on the tensor cores
+  // (split-BF16 slices, FP32 accumulation); the rest in double-float.
+  bool tc_ = !getenv("BDG_GRAM_TC") || atoi(getenv("BDG_GRAM_TC")) != 0;
+  static constexpr long long TC_MIN_ROWS = 2048;
+  bdg_status gram(const PairBlock<R>& A, const PairBlock<R>& B, double* G, bool upper = false,
+                  bool fp32_enough = sizeof(R) == 4) {
+    if (tc_ && fp32_enough && A.n >= TC_MIN_ROWS && gram_tc_supported(A.cols, B.cols)) {
+      BDG_CUDA_TRY(plan_, gram_pairs_tc<R>(A, B, G, gws_, gws_bytes_, s_));
+      return BDG_OK;
+    }
     BDG_CUDA_TRY(plan_, gram_pairs<R>(A, B, G, gws_, gws_bytes_, s_, upper));
     return BDG_OK;
   }
@@ -1015,8 +1028,9 @@ class Solver {
     for (int pass = 0; pass < cgs_passes_; ++pass) {
       double* c1 = dmat_[MAT_G1];
       double* c2 = dmat_[MAT_G2];
-      if ((st = gram(gpart(Bk, 0, bp), fpart(W, 0, wp), c1))) return st;
-      if ((st = gram(fpart(Bk, 0, bp), gpart(W, 0, wp), c2))) return st;
+      const bool first_of_two = pass == 0 && cgs_passes_ >= 2;
+      if ((st = gram(gpart(Bk, 0, bp), fpart(W, 0, wp), c1, false, sizeof(R) == 4 || first_of_two))) return st;
+      if ((st = gram(fpart(Bk, 0, bp), gpart(W, 0, wp), c2, false, sizeof(R) == 4 || first_of_two))) return st;
       if ((st = update_dev(fpart(Bk, 0, bp), c1, nw, 1.0, fptr(W, 0), wp, -1.0))) return st;
       if (HW && (st = update_dev(fpart(HBk, 0, bp), c1, nw, 1.0, fptr(HW, 0), wp, -1.0))) return st;
       if ((st = update_dev(gpart(Bk, 0, bp), c2, nw, 1.0, gptr(W, 0), wp, -1.0))) return st;
@@ -1089,8 +1103,12 @@ class Solver {
       return BDG_ERR_NOMEM;
     }
     owned_.push_back(*p);
+    // diagnostics (BDG_POISON): fill new buffers with NaN bytes, so that a
+    // read before the first write shows up in the results
+    if (poison_ && cudaMemset(*p, 0xFF, bytes) != cudaSuccess) return BDG_ERR_NOMEM;
     return BDG_OK;
   }
+  bool poison_ = getenv("BDG_POISON") != nullptr;
   void release() {
     sec_report();
     if (pinned_) {
@@ -1334,14 +1352,81 @@ extern "C" bdg_status bdg_solve_batched(bdg_plan_t* plans, int count, const int*
     return fail(nullptr, BDG_ERR_INVALID, "plans, k, m, omega and nconv must hold count entries");
   for (int i = 0; i < count; ++i)
     if (!plans[i] || !omega[i]) return fail(nullptr, BDG_ERR_INVALID, "plan or omega entry is NULL");
-  bdg_status first = BDG_OK;
-  for (int i = 0; i < count; ++i) {
-    const bdg_status st = bdg_solve(plans[i], k[i], m[i], nullptr, omega[i], UV ? UV[i] : nullptr,
-                                    resid ? resid[i] : nullptr, &nconv[i], stream);
-    if (st != BDG_OK && first == BDG_OK) {
-      first = st;
+  if (count == 0) return BDG_OK;
+  {
+    std::vector<bdg_plan_t> seen(plans, plans + count);
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+      return fail(nullptr, BDG_ERR_INVALID, "a plan appears twice (its solves would share its scratch)");
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, BDG_ERR_CUDA, "cudaGetDevice failed");
+  for (int i = 0; i < count; ++i)
+    if (bdg_status sd = check_device(plans[i])) {
       set_thread_error("plan " + std::to_string(i) + ": " + plans[i]->err);
+      return sd;
+    }
+  // Work queue over the instances, largest grids first so that the small
+  // ones fill in at the end.  Several host threads take instances from it,
+  // each solving on a stream of its own, so that the kernels of small
+  // instances (which fill a fraction of the SMs) and the host decisions of
+  // one solve overlap with the work of others.  Grids above 2^20 points fill
+  // the GPU alone and are solved one at a time (their banks are large).
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return plans[a]->grid.npts * m[a] > plans[b]->grid.npts * m[b]; });
+  long long biggest = 0;
+  for (int i = 0; i < count; ++i) biggest = std::max(biggest, plans[i]->grid.npts);
+  int workers = getenv("BDG_BATCH_WORKERS") ? atoi(getenv("BDG_BATCH_WORKERS")) : 8;
+  if (biggest > (1LL << 20)) workers = 1;
+  workers = std::max(1, std::min(workers, count));
+  std::vector<bdg_status> st(count, BDG_OK);
+  auto run_one = [&](int i, cudaStream_t s) {
+    st[i] = bdg_solve(plans[i], k[i], m[i], nullptr, omega[i], UV ? UV[i] : nullptr, resid ? resid[i] : nullptr,
+                      &nconv[i], s);
+  };
+  if (workers == 1) {
+    for (int j = 0; j < count; ++j) run_one(order[j], (cudaStream_t)stream);
+  } else {
+    // the workers' streams start after the work already queued on the caller's stream
+    cudaEvent_t ready = nullptr;
+    if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ready, (cudaStream_t)stream) != cudaSuccess)
+      return fail(nullptr, BDG_ERR_CUDA, "event on the caller's stream failed");
+    std::atomic<int> next{0};
+    std::vector<cudaError_t> werr(workers, cudaSuccess);
+    auto work = [&](int w) {
+      cudaStream_t ws = nullptr;
+      cudaError_t e = cudaSetDevice(dev);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(ws, ready, 0);
+      if (e != cudaSuccess) {
+        werr[w] = e;
+        return;
+      }
+      for (int j; (j = next.fetch_add(1)) < count;) run_one(order[j], ws);
+      cudaStreamSynchronize(ws);
+      cudaStreamDestroy(ws);
+    };
+    std::vector<std::thread> pool;
+    for (int w = 0; w < workers; ++w) pool.emplace_back(work, w);
+    for (auto& t : pool) t.join();
+    cudaEventDestroy(ready);
+    // a worker that could not start leaves its instances to the others; the
+    // call fails only if none drained the queue
+    if (next.load() < count) {
+      cudaError_t e = cudaErrorUnknown;
+      for (int w = 0; w < workers; ++w)
+        if (werr[w] != cudaSuccess) e = werr[w];
+      return fail(nullptr, BDG_ERR_CUDA, std::string("no batch worker could start: ") + cudaGetErrorString(e));
     }
   }
+  bdg_status first = BDG_OK;
+  for (int i = 0; i < count; ++i)
+    if (st[i] != BDG_OK && first == BDG_OK) {
+      first = st[i];
+      set_thread_error("plan " + std::to_string(i) + ": " + plans[i]->err);
+    }
   return first;
 }

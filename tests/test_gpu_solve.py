@@ -157,3 +157,36 @@ def test_solve_batched_matches_single_solves():
         assert np.all(resid <= 1e-10)
     for p in plans:
         p.close()
+
+
+def test_solve_batched_work_queue_matches_serial(monkeypatch):
+    """Ten instances of different grids and interactions (16^2 and 32^2, FM
+    and AFM draws) served by four host threads with a stream each give the
+    eigenvalues, residuals and convergence counts of the same call with one
+    worker, and a plan listed twice is refused."""
+    need_torch_cuda()
+    from paper_2506_08308_gb300 import bdg
+    rng = np.random.default_rng(77)
+    cases = []
+    for i in range(10):
+        n = 16 if i % 2 else 32
+        cases.append(synth.Workload(f"q{i}", (n, n), (-6.0, -6.0), (6.0, 6.0), (1.0, 1.3),
+                                    float(rng.uniform(8.0, 20.0)), float(rng.uniform(-2.0, 2.0)), 0.0,
+                                    float(rng.uniform(0.05, 0.4)), k=6, m=10, gs_seed=200 + i, block_seed=300 + i))
+    plans = []
+    for w in cases:
+        V, phi, mu, op = oracle_problem(w)
+        plans.append(make_plan(w, V, phi, prec=bdg.MIXED, tol=1e-10, maxit=600, seed=w.block_seed))
+    ks, ms_ = [w.k for w in cases], [w.m for w in cases]
+    monkeypatch.setenv("BDG_BATCH_WORKERS", "1")
+    serial = bdg.solve_batched(plans, ks, ms_, want_vectors=False)
+    monkeypatch.setenv("BDG_BATCH_WORKERS", "4")
+    queued = bdg.solve_batched(plans, ks, ms_, want_vectors=False)
+    for (om1, _, r1, c1), (om4, _, r4, c4), w in zip(serial, queued, cases):
+        assert c1 == c4 == w.k
+        np.testing.assert_allclose(om4, om1, rtol=1e-12, atol=0)
+        assert np.all(r4 <= 1e-10)
+    with pytest.raises(RuntimeError, match="twice"):
+        bdg.solve_batched([plans[0], plans[1], plans[0]], ks[:3], ms_[:3], want_vectors=False)
+    for p in plans:
+        p.close()

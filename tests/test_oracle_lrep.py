@@ -345,3 +345,29 @@ def test_residuals_closed_forms_on_unconverged_pairs(ground):
         r = both(Fp, G, om)
         expect = e / np.sqrt(np.sum(Fp.reshape(len(om), -1) ** 2, 1) + np.sum(G.reshape(len(om), -1) ** 2, 1))
         np.testing.assert_allclose(r, expect, rtol=1e-6)
+
+
+def test_pair_gram_brute_force_and_complex_identity():
+    """pair_gram against scalar loops over every entry on a tiny block, and
+    against the complex Gram it packs: A^H B = (Re Re + Im Im) + i (Re Im -
+    Im Re) in the 2 x 2 sub-blocks, a transposed operand or a swapped part
+    fails either check."""
+    from oracle import lrep
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((3, 7)) + 1j * rng.standard_normal((3, 7))
+    B = rng.standard_normal((2, 7)) + 1j * rng.standard_normal((2, 7))
+    S, Sabs = lrep.pair_gram(A, B)
+    assert S.shape == (6, 4)
+    for i in range(3):
+        for j in range(2):
+            for s in range(2):
+                for t in range(2):
+                    ref = sum((A[i, r].real if s == 0 else A[i, r].imag) *
+                              (B[j, r].real if t == 0 else B[j, r].imag) for r in range(7))
+                    aref = sum(abs((A[i, r].real if s == 0 else A[i, r].imag) *
+                                   (B[j, r].real if t == 0 else B[j, r].imag)) for r in range(7))
+                    assert abs(S[2 * i + s, 2 * j + t] - ref) < 1e-13
+                    assert abs(Sabs[2 * i + s, 2 * j + t] - aref) < 1e-13
+    H = A.conj() @ B.T
+    np.testing.assert_allclose(S[0::2, 0::2] + S[1::2, 1::2], H.real, atol=1e-13)
+    np.testing.assert_allclose(S[0::2, 1::2] - S[1::2, 0::2], H.imag, atol=1e-13)
