@@ -57,6 +57,9 @@ def parse():
                     help="iteration cap of the FP64-only comparison solve (0: skip)")
     ap.add_argument("--cpu-iters", type=int, default=2,
                     help="oracle solver iterations in the CPU baseline sample (0: skip)")
+    ap.add_argument("--cpu-single-iters", type=int, default=1,
+                    help="oracle iterations of the one-thread CPU sample, run in a child process with every "
+                         "BLAS/OpenMP pool at one thread (0: skip)")
     ap.add_argument("--skip-e2e", action="store_true", help="leave out the host-buffer pass")
     ap.add_argument("--skip-launch-count", action="store_true", help="leave out the profiler pass")
     ap.add_argument("--apply-only", action="store_true",
@@ -248,6 +251,28 @@ def cpu_oracle_sample(iters, inst=None):
                        f"tests/golden/solve_2d_n256.json)"),
             "seconds_per_iteration": per_it,
             "full_solve": {"iterations": n_full, "seconds": gold["solve_seconds"], "cores": gold["cpu_threads"]}}
+
+
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+               "NUMEXPR_NUM_THREADS", "VECLIB_MAXIMUM_THREADS")
+
+
+def cpu_oracle_single(iters):
+    """The same oracle sample with one thread: a child process whose BLAS and
+    OpenMP pools are limited to one thread before numpy loads.  None if the
+    child fails."""
+    env = dict(os.environ)
+    for v in THREAD_VARS:
+        env[v] = "1"
+    code = ("import json, bench; s = bench.cpu_oracle_sample(%d); "
+            "print('CPU1 ' + json.dumps({k: s[k] for k in ('value', 'cores', 'seconds_per_iteration')}))" % iters)
+    try:
+        res = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                             timeout=900)
+    except (OSError, subprocess.TimeoutExpired):
+        return None
+    line = next((x for x in res.stdout.splitlines() if x.startswith("CPU1 ")), None)
+    return json.loads(line[5:]) if line else None
 
 
 def run_reference(args):
@@ -658,6 +683,8 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and args.cpu_iters > 0:
         cpu = cpu_oracle_sample(args.cpu_iters)
+        if args.cpu_single_iters > 0:
+            cpu["one_thread"] = cpu_oracle_single(args.cpu_single_iters)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

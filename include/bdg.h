@@ -148,7 +148,8 @@ bdg_status bdg_biortho(bdg_plan_t plan, int dtype, void* F, void* G, int ncol, c
  *           (BDG_ERR_UNSUPPORTED beyond).
  * Sums are taken in a fixed order (repeated calls give identical G).  The
  * workspace is allocated and freed in stream order on `stream`.
- * ncol_a or ncol_b == 0 is a no-op; n == 0 gives G = 0.
+ * ncol_a or ncol_b == 0 is a no-op; n == 0 gives G = 0 (A and B may then
+ * be NULL).
  */
 typedef enum { BDG_GRAM_SIMT = 0, BDG_GRAM_TENSOR = 1 } bdg_gram_engine;
 bdg_status bdg_gram(int dtype, int engine, const void* A, long long lda, int ncol_a, const void* B, long long ldb,

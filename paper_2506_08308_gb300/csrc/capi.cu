@@ -554,7 +554,7 @@ bdg_status bdg_gram(int dtype, int engine, const void* A, long long lda, int nco
     return fail(nullptr, BDG_ERR_INVALID, "engine must be BDG_GRAM_SIMT or BDG_GRAM_TENSOR");
   if (ncol_a < 0 || ncol_b < 0 || n < 0) return fail(nullptr, BDG_ERR_INVALID, "negative size");
   if (ncol_a == 0 || ncol_b == 0) return BDG_OK;
-  if (!A || !B || !G) return fail(nullptr, BDG_ERR_INVALID, "A, B and G must be device pointers");
+  if (!G || (n > 0 && (!A || !B))) return fail(nullptr, BDG_ERR_INVALID, "A, B and G must be device pointers");
   if ((ncol_a > 1 && lda < n) || (ncol_b > 1 && ldb < n))
     return fail(nullptr, BDG_ERR_INVALID, "column stride below the column length");
   if (engine == BDG_GRAM_TENSOR && !gram_tc_supported(ncol_a, ncol_b))

@@ -260,6 +260,34 @@ class Solver {
     if (alloc(&p, vb * mp_)) return fail(plan_, BDG_ERR_NOMEM, "solver work allocation failed");
     HPb_ = (T*)p;
     big_ = 2 * cap_;
+    bdg_status sl = alloc_lane();
+    if (sl) return sl;
+    if (overlap_) {
+      if (cudaStreamCreateWithFlags(&lane2_.s, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(plan_, BDG_ERR_CUDA, "second solver stream could not be created");
+      }
+      swap_lane(lane2_);
+      sl = alloc_lane();
+      swap_lane(lane2_);
+      if (sl) return sl;
+    }
+    zf_ = (const T*)(sizeof(R) == 8 ? (const void*)plan_->zf64 : (const void*)plan_->zf32);
+    zg_ = (const T*)(sizeof(R) == 8 ? (const void*)plan_->zg64 : (const void*)plan_->zg32);
+    if (inner_steps_ > 0) {
+      auto al = [this](void** q, size_t b) { return alloc(q, b); };
+      bdg_status st = inner_fp32_ ? in32_.init(plan_, mp_, al) : in64_.init(plan_, mp_, al);
+      if (st) return st;
+    }
+    return BDG_OK;
+  }
+
+  // Gram workspace, small matrices, column-norm partials and pinned staging
+  // of the current lane
+  bdg_status alloc_lane() {
+    void* p = nullptr;
     gws_bytes_ = gram_workspace_bytes(cap_, cap_, n3_);
     if (alloc(&p, gws_bytes_)) return fail(plan_, BDG_ERR_NOMEM, "gram workspace allocation failed");
     gws_ = p;
@@ -280,13 +308,7 @@ class Solver {
       pinned_ = nullptr;
       return fail(plan_, BDG_ERR_NOMEM, "pinned staging allocation failed");
     }
-    zf_ = (const T*)(sizeof(R) == 8 ? (const void*)plan_->zf64 : (const void*)plan_->zf32);
-    zg_ = (const T*)(sizeof(R) == 8 ? (const void*)plan_->zg64 : (const void*)plan_->zg32);
-    if (inner_steps_ > 0) {
-      auto al = [this](void** q, size_t b) { return alloc(q, b); };
-      bdg_status st = inner_fp32_ ? in32_.init(plan_, mp_, al) : in64_.init(plan_, mp_, al);
-      if (st) return st;
-    }
+    pin_off_ = 0;
     return BDG_OK;
   }
 
@@ -964,46 +986,69 @@ class Solver {
       HostMat Sel(2 * mmp, 2 * nap);
       for (int jj = 0; jj < na; ++jj) Sel(act[jj], jj) = 1.0;
       if ((st = update_full(Rb_, mmp, Sel, Wb_, nap))) return st;
+      // The previous-update block P (gathered into the second half of W,
+      // Gram-Schmidt against X, bi-orthonormalized behind X) does not depend
+      // on the new directions: with exact images it runs on the second lane
+      // while the inner PCG of the directions runs on this one.
+      const bool fork = overlap_ && lane2_.s && exact_images_ && haveP;
+      if (fork) BDG_CUDA_TRY(plan_, cudaEventRecord(ev_fork_, s_));
       { int si_; cudaEvent_t se_ = sec_begin("inner directions", &si_); st = directions(Wb_, nap); sec_end(se_); if (st) return st; }
+      int nw = 2 * nap;
+      int rp = 0;
+      T* const HWx = exact_images_ ? nullptr : HWb_;   // images carried only without exact products
+      auto p_chain = [&]() -> bdg_status {
+        bdg_status sp = BDG_OK;
+        if (haveP) {
+          // previous-update columns that carry information: |P_j| >= 1e-12 |X_j|
+          // (near convergence P is a cancellation-level difference whose image
+          // is consistent with it only to eps |X| / |P|; such columns are left out)
+          std::vector<double> npn;
+          if ((sp = colnorms(Pb_, mmp, npn))) return sp;
+          std::vector<int> actp;
+          for (int j : act)
+            if (npn[j] >= 1e-24 * nx[j]) actp.push_back(j);
+          const int npa = (int)actp.size();
+          if (npa > 0) {
+            HostMat SelP(2 * mmp, 2 * nap);
+            for (int jj = 0; jj < npa; ++jj) SelP(actp[jj], jj) = 1.0;
+            if ((sp = update_full(Pb_, mmp, SelP, Wb_ + (long long)nap * vlen_, nap))) return sp;
+            if (!exact_images_ && (sp = update_full(HPb_, mmp, SelP, HWb_ + (long long)nap * vlen_, nap)))
+              return sp;
+            nw = 4 * nap;
+          }
+        }
+        // Bi-orthogonal Gram-Schmidt in two stages: P against X, then
+        // bi-orthonormalize P; D against [X, P'], then bi-orthonormalize D.
+        // Each block holds at most 2 nap columns, so its Jordan-Wielandt
+        // problem stays within the projected solver's size.
+        if (nw > 2 * nap) {
+          T* WP = Wb_ + (long long)nap * vlen_;
+          T* HWP = HWx ? HWx + (long long)nap * vlen_ : nullptr;
+          { int si_; cudaEvent_t se_ = sec_begin("cgs2 P", &si_); sp = cgs2(X, HX, mmp, WP, HWP, nap); sec_end(se_); if (sp) return sp; }
+          { int si_; cudaEvent_t se_ = sec_begin("biortho P", &si_);
+            sp = biortho_block(WP, HWP, nap, 2 * nap, fptr(X, mmp), HWP ? fptr(HX, mmp) : nullptr, rtol_, &rp);
+            sec_end(se_); if (sp) return sp; }
+        }
+        return BDG_OK;
+      };
+      if (fork) {
+        BDG_CUDA_TRY(plan_, cudaStreamWaitEvent(lane2_.s, ev_fork_, 0));
+        {
+          swap_lane(lane2_);
+          LaneGuard back{this};
+          st = p_chain();
+          if (!st && cudaEventRecord(ev_join_, s_) != cudaSuccess) st = fail(plan_, BDG_ERR_CUDA, "join event");
+        }
+        if (st) return st;
+        BDG_CUDA_TRY(plan_, cudaStreamWaitEvent(s_, ev_join_, 0));
+      }
       { int si_; cudaEvent_t se_ = sec_begin("deflate D", &si_); st = deflate(Wb_, 0, nap); sec_end(se_); if (st) return st; }
       // unit f- and g-parts before the product: the two real columns sharing
       // a complex vector then have equal norms, so the rounding crosstalk
       // between them in the FFTs stays at eps relative to each column
       { int si_; cudaEvent_t se_ = sec_begin("normalize D", &si_); st = normalize_parts(Wb_, nullptr, nap); sec_end(se_); if (st) return st; }
       if (!exact_images_ && (st = apply_fg(Wb_, HWb_, nap))) return st;
-      int nw = 2 * nap;
-      if (haveP) {
-        // previous-update columns that carry information: |P_j| >= 1e-12 |X_j|
-        // (near convergence P is a cancellation-level difference whose image
-        // is consistent with it only to eps |X| / |P|; such columns are left out)
-        std::vector<double> npn;
-        if ((st = colnorms(Pb_, mmp, npn))) return st;
-        std::vector<int> actp;
-        for (int j : act)
-          if (npn[j] >= 1e-24 * nx[j]) actp.push_back(j);
-        const int npa = (int)actp.size();
-        if (npa > 0) {
-          HostMat SelP(2 * mmp, 2 * nap);
-          for (int jj = 0; jj < npa; ++jj) SelP(actp[jj], jj) = 1.0;
-          if ((st = update_full(Pb_, mmp, SelP, Wb_ + (long long)nap * vlen_, nap))) return st;
-          if (!exact_images_ && (st = update_full(HPb_, mmp, SelP, HWb_ + (long long)nap * vlen_, nap))) return st;
-          nw = 4 * nap;
-        }
-      }
-      // Bi-orthogonal Gram-Schmidt in two stages: P against X, then
-      // bi-orthonormalize P; D against [X, P'], then bi-orthonormalize D.
-      // Each block holds at most 2 nap columns, so its Jordan-Wielandt
-      // problem stays within the projected solver's size.
-      int rp = 0;
-      T* const HWx = exact_images_ ? nullptr : HWb_;   // images carried only without exact products
-      if (nw > 2 * nap) {
-        T* WP = Wb_ + (long long)nap * vlen_;
-        T* HWP = HWx ? HWx + (long long)nap * vlen_ : nullptr;
-        { int si_; cudaEvent_t se_ = sec_begin("cgs2 P", &si_); st = cgs2(X, HX, mmp, WP, HWP, nap); sec_end(se_); if (st) return st; }
-        { int si_; cudaEvent_t se_ = sec_begin("biortho P", &si_);
-          st = biortho_block(WP, HWP, nap, 2 * nap, fptr(X, mmp), HWP ? fptr(HX, mmp) : nullptr, rtol_, &rp);
-          sec_end(se_); if (st) return st; }
-      }
+      if (!fork && (st = p_chain())) return st;
       const int rpp = (rp + 1) / 2;
       { int si_; cudaEvent_t se_ = sec_begin("cgs2 D", &si_); st = cgs2(X, HX, mmp + rpp, Wb_, HWx, nap); sec_end(se_); if (st) return st; }
       int rd = 0;
@@ -1116,6 +1161,18 @@ class Solver {
       cudaFreeHost(pinned_);
       pinned_ = nullptr;
     }
+    if (lane2_.s) {
+      cudaStreamSynchronize(lane2_.s);
+      cudaStreamDestroy(lane2_.s);
+      lane2_.s = nullptr;
+    }
+    if (lane2_.pinned) {
+      cudaFreeHost(lane2_.pinned);
+      lane2_.pinned = nullptr;
+    }
+    if (ev_fork_) cudaEventDestroy(ev_fork_);
+    if (ev_join_) cudaEventDestroy(ev_join_);
+    ev_fork_ = ev_join_ = nullptr;
     for (void* p : owned_) cudaFree(p);
     owned_.clear();
   }
@@ -1146,6 +1203,44 @@ class Solver {
   static constexpr size_t PIN_DOUBLES = 1 << 20;   // 8 MB of pinned staging
   double* pinned_ = nullptr;
   size_t pin_off_ = 0;
+  // A second lane -- a stream of its own with its own Gram workspace, small
+  // matrices, column-norm partials and pinned staging -- runs the
+  // previous-update block's Gram-Schmidt while the inner PCG of the new
+  // directions runs on the solver's stream (BDG_OVERLAP=0 keeps one lane).
+  // The two chains touch disjoint buffers, so the results do not change.
+  struct Lane {
+    cudaStream_t s = nullptr;
+    void* gws = nullptr;
+    size_t gws_bytes = 0;
+    double* dsm = nullptr;
+    double* dmat[NMAT] = {};
+    double* dvec = nullptr;
+    double* dws = nullptr;
+    double* cnpart = nullptr;
+    int* dint = nullptr;
+    double* pinned = nullptr;
+    size_t pin_off = 0;
+  };
+  Lane lane2_;
+  bool overlap_ = !getenv("BDG_OVERLAP") || atoi(getenv("BDG_OVERLAP")) != 0;
+  cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
+  void swap_lane(Lane& L) {
+    std::swap(s_, L.s);
+    std::swap(gws_, L.gws);
+    std::swap(gws_bytes_, L.gws_bytes);
+    std::swap(dsm_, L.dsm);
+    for (int i = 0; i < NMAT; ++i) std::swap(dmat_[i], L.dmat[i]);
+    std::swap(dvec_, L.dvec);
+    std::swap(dws_, L.dws);
+    std::swap(cnpart_, L.cnpart);
+    std::swap(dint_, L.dint);
+    std::swap(pinned_, L.pinned);
+    std::swap(pin_off_, L.pin_off);
+  }
+  struct LaneGuard {
+    Solver* S;
+    ~LaneGuard() { S->swap_lane(S->lane2_); }
+  };
   int big_ = 0;
   bool dbg_eigh_ = getenv("BDG_CHECK_EIGH") != nullptr;
   T* dbg_buf_ = nullptr;
@@ -1385,6 +1480,9 @@ extern "C" bdg_status bdg_solve_batched(bdg_plan_t* plans, int count, const int*
   auto run_one = [&](int i, cudaStream_t s) {
     st[i] = bdg_solve(plans[i], k[i], m[i], nullptr, omega[i], UV ? UV[i] : nullptr, resid ? resid[i] : nullptr,
                       &nconv[i], s);
+    // bdg_solve has synchronized its stream; the plan must not keep a
+    // worker's stream, which is destroyed when the worker ends
+    plans[i]->last_stream = stream;
   };
   if (workers == 1) {
     for (int j = 0; j < count; ++j) run_one(order[j], (cudaStream_t)stream);
