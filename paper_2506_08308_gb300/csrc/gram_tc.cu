@@ -143,14 +143,21 @@ __device__ __forceinline__ void stage_rows(const PairBlock<R>& X, int col, long 
   }
   const uint32_t slice_bytes = (uint32_t)tcols * TBK * 2;
   const uint32_t lbo = (uint32_t)(tcols / 8) * 128;
+  // The eight threads of a quarter warp hold eight consecutive complex
+  // columns of one K group: those with complex column % 8 >= 4 store the
+  // imaginary row first, so that every 16-byte store of the quarter warp
+  // lands in a different group of four banks.
+  const int flip = (c >> 3) & 1;
 #pragma unroll
-  for (int part = 0; part < 2; ++part) {
+  for (int q = 0; q < 2; ++q) {
+    const int part = q ^ flip;
     const int cc = c + part;
     const uint32_t off = (uint32_t)g * lbo + (uint32_t)(cc / 8) * 128 + (uint32_t)(cc % 8) * 16;
 #pragma unroll
     for (int s = 0; s < NSLICE; ++s) {
-      uint4 u = make_uint4(w[part][s][0], w[part][s][1], w[part][s][2], w[part][s][3]);
-      *reinterpret_cast<uint4*>(base + s * slice_bytes + off) = u;
+      const uint4 u0 = make_uint4(w[0][s][0], w[0][s][1], w[0][s][2], w[0][s][3]);
+      const uint4 u1 = make_uint4(w[1][s][0], w[1][s][1], w[1][s][2], w[1][s][3]);
+      *reinterpret_cast<uint4*>(base + s * slice_bytes + off) = part ? u1 : u0;
     }
   }
 }
@@ -198,10 +205,17 @@ __global__ void __launch_bounds__(TTHREADS, 2)
     // the MMAs that read this stage (committed TSTAGES steps ago) are done
     if (step >= TSTAGES && !mbar_wait(smem_u32(&mbar[st]), (uint32_t)((step / TSTAGES - 1) & 1))) lost = true;
     const long long r0 = r_begin + (long long)step * TBK;
-    // A: 64 complex columns x 4 groups of 8 rows, one group per thread
-    stage_rows<R>(A, i0 / 2 + (tid >> 2), r0 + 8 * (tid & 3), r_end, 2 * (tid >> 2), tid & 3, TM, sa);
-    for (int t = tid; t < (NT / 2) * 4; t += TTHREADS)
-      stage_rows<R>(B, t >> 2, r0 + 8 * (t & 3), r_end, 2 * (t >> 2), t & 3, NT, sb);
+    // A: 64 complex columns x 4 groups of 8 rows, one group per thread;
+    // task t -> column (t & 7) + 8 (t >> 5), group (t >> 3) & 3: a quarter
+    // warp covers eight consecutive columns of one group
+    {
+      const int c = (tid & 7) | ((tid >> 5) << 3), g = (tid >> 3) & 3;
+      stage_rows<R>(A, i0 / 2 + c, r0 + 8 * g, r_end, 2 * c, g, TM, sa);
+    }
+    for (int t = tid; t < (NT / 2) * 4; t += TTHREADS) {
+      const int c = (t & 7) | ((t >> 5) << 3), g = (t >> 3) & 3;
+      stage_rows<R>(B, c, r0 + 8 * g, r_end, 2 * c, g, NT, sb);
+    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {

@@ -1076,6 +1076,10 @@ class Solver {
       const bool first_of_two = pass == 0 && cgs_passes_ >= 2;
       if ((st = gram(gpart(Bk, 0, bp), fpart(W, 0, wp), c1, false, sizeof(R) == 4 || first_of_two))) return st;
       if ((st = gram(fpart(Bk, 0, bp), gpart(W, 0, wp), c2, false, sizeof(R) == 4 || first_of_two))) return st;
+      // (the updates stay in double-float in both passes: rounding errors of
+      // an FP32 update lie outside span(B), where the second pass cannot
+      // remove them, and near convergence W is mostly along B, so they
+      // swamp its remaining part -- tried, and the solves stalled)
       if ((st = update_dev(fpart(Bk, 0, bp), c1, nw, 1.0, fptr(W, 0), wp, -1.0))) return st;
       if (HW && (st = update_dev(fpart(HBk, 0, bp), c1, nw, 1.0, fptr(HW, 0), wp, -1.0))) return st;
       if ((st = update_dev(gpart(Bk, 0, bp), c2, nw, 1.0, gptr(W, 0), wp, -1.0))) return st;
