@@ -12,6 +12,7 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int NQ_MAX = 8;   // reduced quantities per complex column: 4 CG sums, or 4 Z columns x (re, im)
+static_assert(NQ_MAX <= NT / 32, "sum_partials gives every quantity a warp");
 
 // Block-wide sum of nq per-thread values in FP64, deterministic (fixed
 // shuffle tree, then warps in order); the result lands in out[0..nq) of
@@ -35,17 +36,16 @@ __device__ __forceinline__ void block_sum(double (&v)[NQ], int nq, double* red /
 
 // out[q] = sum over the nchunk partials of quantity q of complex column
 // `pair` (layout part[(pair * nchunk + chunk) * nq + q]), in a fixed order:
-// warp 0, lane l sums chunks l, l + 32, ..., then a shuffle tree.
+// warp q, lane l sums chunks l, l + 32, ..., then a shuffle tree (the nq <=
+// NT / 32 quantities in parallel, one warp each).
 __device__ __forceinline__ void sum_partials(const double* __restrict__ part, int pair, int nchunk, int nq,
                                              double* out) {
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int q = 0; q < nq; ++q) {
-      double t = 0.0;
-      for (int c = lane; c < nchunk; c += 32) t += part[((long long)pair * nchunk + c) * nq + q];
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) out[q] = t;
-    }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < nq) {
+    double t = 0.0;
+    for (int c = lane; c < nchunk; c += 32) t += part[((long long)pair * nchunk + c) * nq + warp];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) out[warp] = t;
   }
   __syncthreads();
 }

@@ -265,7 +265,8 @@ class Solver {
     if (overlap_) {
       if (cudaStreamCreateWithFlags(&lane2_.s, cudaStreamNonBlocking) != cudaSuccess ||
           cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming) != cudaSuccess) {
+          cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ev_img_, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         return fail(plan_, BDG_ERR_CUDA, "second solver stream could not be created");
       }
@@ -991,6 +992,7 @@ class Solver {
       // on the new directions: with exact images it runs on the second lane
       // while the inner PCG of the directions runs on this one.
       const bool fork = overlap_ && lane2_.s && exact_images_ && haveP;
+      bool p_images = false;   // images of P' formed on the second lane
       if (fork) BDG_CUDA_TRY(plan_, cudaEventRecord(ev_fork_, s_));
       { int si_; cudaEvent_t se_ = sec_begin("inner directions", &si_); st = directions(Wb_, nap); sec_end(se_); if (st) return st; }
       int nw = 2 * nap;
@@ -1038,6 +1040,17 @@ class Solver {
           LaneGuard back{this};
           st = p_chain();
           if (!st && cudaEventRecord(ev_join_, s_) != cudaSuccess) st = fail(plan_, BDG_ERR_CUDA, "join event");
+          // the images of P' need nothing from the directions either: their
+          // product also runs on this lane, joined before the next
+          // Rayleigh-Ritz step
+          if (!st && rp > 0) {
+            int si_;
+            cudaEvent_t se_ = sec_begin("apply new columns P", &si_);
+            st = apply_fg(fptr(X, mmp), fptr(HX, mmp), (rp + 1) / 2);
+            sec_end(se_);
+            if (!st && cudaEventRecord(ev_img_, s_) != cudaSuccess) st = fail(plan_, BDG_ERR_CUDA, "image event");
+            p_images = !st;
+          }
         }
         if (st) return st;
         BDG_CUDA_TRY(plan_, cudaStreamWaitEvent(s_, ev_join_, 0));
@@ -1058,7 +1071,18 @@ class Solver {
       if (log_) fprintf(stderr, "[bdg]   block ranks P %d D %d\n", rp, rd);
       if (rp + rd == 0) return fail(plan_, BDG_ERR_BREAKDOWN, "search directions lost rank");
       // images of the new basis columns [P', D'] by one product
-      if (exact_images_) { int si_; cudaEvent_t se_ = sec_begin("apply new columns", &si_); st = apply_fg(fptr(X, mmp), fptr(HX, mmp), rpp + (rd + 1) / 2); sec_end(se_); if (st) return st; }
+      if (exact_images_) {
+        int si_;
+        cudaEvent_t se_ = sec_begin("apply new columns", &si_);
+        if (p_images) {
+          st = apply_fg(fptr(X, mmp + rpp), fptr(HX, mmp + rpp), (rd + 1) / 2);
+          if (!st && cudaStreamWaitEvent(s_, ev_img_, 0) != cudaSuccess) st = fail(plan_, BDG_ERR_CUDA, "image join");
+        } else {
+          st = apply_fg(fptr(X, mmp), fptr(HX, mmp), rpp + (rd + 1) / 2);
+        }
+        sec_end(se_);
+        if (st) return st;
+      }
       nxb = 2 * mmp;
       nu = 2 * (mmp + rpp) + rd;
     }
@@ -1176,7 +1200,8 @@ class Solver {
     }
     if (ev_fork_) cudaEventDestroy(ev_fork_);
     if (ev_join_) cudaEventDestroy(ev_join_);
-    ev_fork_ = ev_join_ = nullptr;
+    if (ev_img_) cudaEventDestroy(ev_img_);
+    ev_fork_ = ev_join_ = ev_img_ = nullptr;
     for (void* p : owned_) cudaFree(p);
     owned_.clear();
   }
@@ -1227,7 +1252,7 @@ class Solver {
   };
   Lane lane2_;
   bool overlap_ = !getenv("BDG_OVERLAP") || atoi(getenv("BDG_OVERLAP")) != 0;
-  cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
+  cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr, ev_img_ = nullptr;
   void swap_lane(Lane& L) {
     std::swap(s_, L.s);
     std::swap(gws_, L.gws);
