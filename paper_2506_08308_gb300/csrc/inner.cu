@@ -198,20 +198,42 @@ __global__ void __launch_bounds__(NT) k_zsub(typename CT<R>::T* __restrict__ v, 
   const int pair = blockIdx.y;
   sum_partials(part, pair, nchunk, NQ_MAX, cf);
   const long long vlen = 2 * n3, off = (long long)pair * vlen;
-  for (long long e = (long long)blockIdx.x * NT + threadIdx.x; e < vlen; e += (long long)gridDim.x * NT) {
-    T x = v[off + e];
-    if (e < n3) {
-      if (nzg > 0) {
-        const R zv = zg[e].x;
-        x = mk(fma(-zv, (R)cf[0], x.x), fma(-zv, (R)cf[1], x.y));
-      }
-    } else {
-      for (int c = 0; c < nzf; ++c) {
-        const R zv = zf[c * n3 + (e - n3)].x;
-        x = mk(fma(-zv, (R)cf[2 + 2 * c], x.x), fma(-zv, (R)cf[3 + 2 * c], x.y));
+  const long long stride = (long long)gridDim.x * NT;
+  // ZB elements per thread and batch, all loads of a batch issued before its
+  // stores (a load after a store to v could not be moved ahead of it)
+  constexpr int ZB = 4;
+  for (long long e0 = (long long)blockIdx.x * NT + threadIdx.x; e0 < vlen; e0 += ZB * stride) {
+    T x[ZB];
+    R z[ZB][3];
+#pragma unroll
+    for (int b = 0; b < ZB; ++b) {
+      const long long e = e0 + b * stride;
+      x[b] = mk((R)0, (R)0);
+      z[b][0] = z[b][1] = z[b][2] = (R)0;
+      if (e >= vlen) continue;
+      x[b] = v[off + e];
+      if (e < n3) {
+        if (nzg > 0) z[b][0] = zg[e].x;
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (c < nzf) z[b][c] = zf[c * n3 + (e - n3)].x;
       }
     }
-    v[off + e] = x;
+#pragma unroll
+    for (int b = 0; b < ZB; ++b) {
+      const long long e = e0 + b * stride;
+      if (e >= vlen) continue;
+      T y = x[b];
+      if (e < n3) {
+        if (nzg > 0) y = mk(fma(-z[b][0], (R)cf[0], y.x), fma(-z[b][0], (R)cf[1], y.y));
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (c < nzf) y = mk(fma(-z[b][c], (R)cf[2 + 2 * c], y.x), fma(-z[b][c], (R)cf[3 + 2 * c], y.y));
+      }
+      v[off + e] = y;
+    }
   }
 }
 
