@@ -1,4 +1,5 @@
 // Inner PCG of the subspace iteration's search directions (see inner.cuh).
+#include <cstdlib>
 #include <string>
 
 #include "blas.cuh"
@@ -281,11 +282,68 @@ bdg_status InnerPCG<RI>::precondition(const T* x, T* y, int pairs, double sigma,
 }
 
 template <typename RI>
+void InnerPCG<RI>::release_graphs() {
+  for (auto& g : graphs_)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  graphs_.clear();
+  if (cap_) cudaStreamDestroy(cap_);
+  cap_ = nullptr;
+}
+
+template <typename RI>
 template <typename R>
 bdg_status InnerPCG<RI>::run(const typename CT<R>::T* Rin, typename CT<R>::T* D, int pairs, int steps,
                              double sigma, cudaStream_t s) {
   if (pairs <= 0) return BDG_OK;
   if (pairs > max_pairs_) return fail(plan_, BDG_ERR_INVALID, "inner solver: block wider than its buffers");
+  // products issued per call: one per step on the pairs, both halves
+  if (sizeof(RI) == 8) plan_->stats.applies_fp64 += 2 * pairs * steps;
+  else plan_->stats.applies_fp32 += 2 * pairs * steps;
+  // graphs pay where launches are many and kernels short enough for the
+  // host's launch time to matter: grids of 2^16 points and more
+  const bool graphs_env = !getenv("BDG_INNER_GRAPHS") || atoi(getenv("BDG_INNER_GRAPHS")) != 0;
+  if (!graphs_env || !use_graphs_ || np_ < (1LL << 16)) return run_direct<R>(Rin, D, pairs, steps, sigma, s);
+  Graph* g = nullptr;
+  for (auto& e : graphs_)
+    if (e.rin == (const void*)Rin && e.d == (const void*)D && e.pairs == pairs && e.steps == steps &&
+        e.sigma == sigma && e.rbytes == (int)sizeof(R))
+      g = &e;
+  if (!g) {
+    graphs_.push_back(Graph{Rin, D, pairs, steps, (int)sizeof(R), sigma, nullptr, false});
+    return run_direct<R>(Rin, D, pairs, steps, sigma, s);
+  }
+  if (g->direct) return run_direct<R>(Rin, D, pairs, steps, sigma, s);
+  if (!g->exec) {
+    if (!cap_ && cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      use_graphs_ = false;
+      return run_direct<R>(Rin, D, pairs, steps, sigma, s);
+    }
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    bdg_status st = BDG_OK;
+    if (ok) {
+      st = run_direct<R>(Rin, D, pairs, steps, sigma, cap_);
+      ok = cudaStreamEndCapture(cap_, &graph) == cudaSuccess && st == BDG_OK && graph;
+    }
+    if (ok) ok = cudaGraphInstantiate(&g->exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+      cudaGetLastError();
+      if (g->exec) cudaGraphExecDestroy(g->exec);
+      g->exec = nullptr;
+      g->direct = true;
+      return run_direct<R>(Rin, D, pairs, steps, sigma, s);
+    }
+  }
+  BDG_CUDA_TRY(plan_, cudaGraphLaunch(g->exec, s));
+  return BDG_OK;
+}
+
+template <typename RI>
+template <typename R>
+bdg_status InnerPCG<RI>::run_direct(const typename CT<R>::T* Rin, typename CT<R>::T* D, int pairs, int steps,
+                                    double sigma, cudaStream_t s) {
   T *x = buf_[0], *r = buf_[1], *z = buf_[2], *p = buf_[3], *q = buf_[4];
   const long long n3 = 3 * np_;
   const dim3 rows(row_blocks(vlen_), pairs);
@@ -301,8 +359,6 @@ bdg_status InnerPCG<RI>::run(const typename CT<R>::T* Rin, typename CT<R>::T* D,
     double* rz_cur = rz_ + (it & 1) * 4 * max_pairs_;
     double* rz_nxt = rz_ + ((it + 1) & 1) * 4 * max_pairs_;
     if ((st = apply_internal(plan_, BDG_FG, dtype, p, q, pairs, s, nullptr))) return st;
-    if (sizeof(RI) == 8) plan_->stats.applies_fp64 += 2 * pairs;
-    else plan_->stats.applies_fp32 += 2 * pairs;
     if ((st = dots(p, q, pairs, s))) return st;
     k_cg_xr<RI><<<rows, NT, 0, s>>>(x, r, p, q, n3, nchunk_, part_, rz_cur, it == 0 ? 1 : 0);
     BDG_CUDA_TRY(plan_, cudaGetLastError());
@@ -323,6 +379,9 @@ bdg_status InnerPCG<RI>::run(const typename CT<R>::T* Rin, typename CT<R>::T* D,
 
 template class InnerPCG<float>;
 template class InnerPCG<double>;
+template bdg_status InnerPCG<float>::run_direct<float>(const float2*, float2*, int, int, double, cudaStream_t);
+template bdg_status InnerPCG<float>::run_direct<double>(const double2*, double2*, int, int, double, cudaStream_t);
+template bdg_status InnerPCG<double>::run_direct<double>(const double2*, double2*, int, int, double, cudaStream_t);
 template bdg_status InnerPCG<float>::run<float>(const float2*, float2*, int, int, double, cudaStream_t);
 template bdg_status InnerPCG<float>::run<double>(const double2*, double2*, int, int, double, cudaStream_t);
 template bdg_status InnerPCG<double>::run<double>(const double2*, double2*, int, int, double, cudaStream_t);

@@ -23,6 +23,8 @@
 // plain FP64 solver.
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace bdg {
@@ -59,9 +61,17 @@ class InnerPCG {
   // D (outer precision R, pairs complex columns, column stride 6 N_p) =
   // steps PCG steps on the systems above with right-hand sides Rin (same
   // layout; Rin may equal D).  sigma is the shift of T_sigma.
+  //
+  // The steps issue about ten launches each and take no host decision, so
+  // on large grids a call repeated with the same buffers, block width,
+  // steps and shift replays a CUDA graph captured on its second occurrence
+  // (the first runs directly and sets every kernel's launch attributes).
+  // A capture that fails falls back to direct launches.
   template <typename R>
   bdg_status run(const typename CT<R>::T* Rin, typename CT<R>::T* D, int pairs, int steps, double sigma,
                  cudaStream_t s);
+
+  ~InnerPCG() { release_graphs(); }
 
   static int chunks_for(long long vlen) {
     long long c = (vlen + 8191) / 8192;   // about 8192 values per CTA and column
@@ -70,6 +80,22 @@ class InnerPCG {
   }
 
  private:
+  template <typename R>
+  bdg_status run_direct(const typename CT<R>::T* Rin, typename CT<R>::T* D, int pairs, int steps, double sigma,
+                        cudaStream_t s);
+  void release_graphs();
+  struct Graph {
+    const void* rin;
+    const void* d;
+    int pairs, steps, rbytes;
+    double sigma;
+    cudaGraphExec_t exec;  // null until captured
+    bool direct;           // capture failed: launch directly
+  };
+  std::vector<Graph> graphs_;
+  cudaStream_t cap_ = nullptr;   // private stream the graphs are captured on
+  bool use_graphs_ = true;
+
   bdg_status deflate_swapped(T* v, int pairs, cudaStream_t s);
   bdg_status dots(const T* a, const T* b, int pairs, cudaStream_t s);
   bdg_status precondition(const T* x, T* y, int pairs, double sigma, cudaStream_t s);

@@ -83,3 +83,28 @@ def test_solve_2d_n32_block48_against_dense(prec):
     plan.close()
     assert nconv == W32.k and np.all(resid <= 1e-10), resid
     _checks(W32, op, om, UV, om_d)
+
+
+def test_inner_graph_replay_gives_identical_results(monkeypatch):
+    """On the 256^2 grid the inner PCG of the search directions replays CUDA
+    graphs captured on the second call of each block width: eigenvalues,
+    residuals, iteration counts and vectors equal those of direct launches
+    (BDG_INNER_GRAPHS=0) bit for bit, in mixed and FP64 precision."""
+    torch = need_torch_cuda()
+    from paper_2506_08308_gb300 import bdg
+    with open(os.path.join(HERE, "golden", "solve_2d_n256.json")) as fh:
+        gold = json.load(fh)
+    V, phi, mu, op = _oracle_2d_n256(gold)
+    X0 = torch.from_numpy(synth.random_block(W, 12, complex_=True)).cuda()
+    for prec in (bdg.MIXED, bdg.FP64):
+        plan = make_plan(W, V, phi, prec=prec, tol=1e-10, maxit=600)
+        out = {}
+        for graphs in ("0", "1"):
+            monkeypatch.setenv("BDG_INNER_GRAPHS", graphs)
+            om, UV, resid, nconv = plan.solve(8, 12, X0=X0)
+            out[graphs] = (om.copy(), resid.copy(), nconv, plan.stats()["iterations"], UV.cpu().numpy())
+        plan.close()
+        assert out["0"][2] == out["1"][2] == 8
+        assert out["0"][3] == out["1"][3]
+        for a, b in zip(out["0"][:2] + out["0"][4:], out["1"][:2] + out["1"][4:]):
+            assert np.array_equal(a, b)
