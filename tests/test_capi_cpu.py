@@ -141,3 +141,36 @@ def test_binding_checks_blocks_before_the_library():
     for kw in ({"Gl": cpu}, {"Fl": cpu}):
         with pytest.raises(ValueError, match="Fl and Gl go together"):
             p.biortho(cpu, cpu.clone(), **kw)
+
+
+def test_gram_and_batched_checks_on_the_host(lib):
+    """bdg_gram refuses a bad dtype or engine, negative sizes, a column stride
+    below the column length, NULL blocks with rows to sum and a tensor-core
+    B block wider than 160 real columns, and is a no-op for empty blocks;
+    bdg_solve_batched refuses NULL arrays; the binding checks the blocks'
+    types and shapes before calling the library.  None of this touches a
+    device."""
+    import numpy as np
+    import torch
+    from paper_2506_08308_gb300 import bdg
+    G = np.zeros(64)
+    g = bdg._dptr(G)
+    one = ctypes.c_void_p(1)   # never dereferenced: every case below fails before device work
+    assert lib.bdg_gram(7, bdg.GRAM_SIMT, one, 10, 2, one, 10, 2, 10, g, None) == bdg.ERR_INVALID
+    assert lib.bdg_gram(bdg.C128, 5, one, 10, 2, one, 10, 2, 10, g, None) == bdg.ERR_INVALID
+    assert lib.bdg_gram(bdg.C128, bdg.GRAM_SIMT, one, 10, -1, one, 10, 2, 10, g, None) == bdg.ERR_INVALID
+    assert lib.bdg_gram(bdg.C128, bdg.GRAM_SIMT, one, 5, 2, one, 10, 2, 10, g, None) == bdg.ERR_INVALID
+    assert lib.bdg_gram(bdg.C128, bdg.GRAM_SIMT, None, 10, 2, one, 10, 2, 10, g, None) == bdg.ERR_INVALID
+    assert lib.bdg_gram(bdg.C64, bdg.GRAM_TENSOR, one, 10, 2, one, 10, 81, 10, g, None) == bdg.ERR_UNSUPPORTED
+    assert lib.bdg_gram(bdg.C128, bdg.GRAM_SIMT, None, 0, 0, None, 0, 3, 10, g, None) == bdg.OK
+    nconv = (ctypes.c_int * 1)()
+    assert lib.bdg_solve_batched(None, 1, None, None, None, None, None, nconv, None) == bdg.ERR_INVALID
+    assert lib.bdg_solve_batched(None, 0, None, None, None, None, None, None, None) == bdg.OK
+    A = torch.zeros((2, 8), dtype=torch.complex64)
+    B = torch.zeros((2, 8), dtype=torch.complex128)
+    with pytest.raises(ValueError):
+        bdg.gram(A, B)                      # mixed dtypes
+    with pytest.raises(ValueError):
+        bdg.gram(A, A[:, :4])               # different column lengths
+    with pytest.raises(ValueError):
+        bdg.gram(A, A)                      # host tensors
