@@ -650,7 +650,7 @@ def run_ours(args):
 
     # ---- kernel launches and per-kernel device time of one solve, from a
     # CUPTI trace (torch profiler) over one extra, untimed step
-    launches, shares = None, None
+    launches, shares, dominant = None, None, None
     if not args.skip_launch_count:
         try:
             from torch.profiler import ProfilerActivity, profile
@@ -683,6 +683,21 @@ def run_ours(args):
                 shares = {"step_device_ms": total / 1000.0, "launches_per_step": n,
                           "kernels": [{"name": k, "launches": c, "ms": t / 1000.0, "share": t / total}
                                       for k, (c, t) in top]}
+                # roofline of the step's dominant kernel, the double-float block
+                # update: its algorithmic FLOPs in the profiled solve (counted by
+                # the library) over its device time in the trace, against the
+                # FP32 SIMT peak divided by the 15 FP32 operations of one
+                # double-float multiply-add
+                upd = per_kernel.get("k_update_df")
+                fl = plan.stats().get("flops_update_df", 0.0)
+                if upd and upd[1] > 0 and fl > 0:
+                    ach = fl / (upd[1] / 1e6) / 1e12
+                    pk = 152 * 128 * 2 * ((clocks or {}).get("sm_max_mhz") or 2070.0) * 1e6 / 1e12 / 15.0
+                    dominant = {"kernel": "k_update_df (FP64 block update in double-float)", "share": upd[1] / total,
+                                "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                                "traffic": None,
+                                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x SM clock / 15 FP32 "
+                                             "operations per double-float multiply-add"}
         except Exception as exc:  # noqa: BLE001 -- auxiliary evidence only
             launches, shares = None, {"error": f"{type(exc).__name__}: {exc}"[:300]}
 
@@ -703,6 +718,7 @@ def run_ours(args):
                                    "no flush") if w.npts >= 65536 else "L2-resident problem; no flush",
                                parallelism=f"{world} independent instance(s)"),
                 "roofline": roofline,
+                "roofline_dominant": dominant,
                 "cpu_baseline": cpu,
                 "e2e": e2e,
                 "fp64_solver": fp64,

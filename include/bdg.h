@@ -206,6 +206,8 @@ typedef struct {
   int applies_fp32;        /* vector-products in FP32 */
   int applies_fp64;        /* vector-products in FP64 */
   double seconds;          /* wall time of the call */
+  double flops_update_df;  /* algorithmic FLOPs (2 per multiply-add) of the FP64 block
+                              updates, which run in double-float arithmetic */
 } bdg_solve_stats;
 bdg_status bdg_get_solve_stats(bdg_plan_t plan, bdg_solve_stats* st);
 

@@ -47,7 +47,7 @@ class Params(ctypes.Structure):
 class SolveStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("iterations_fp32", ctypes.c_int),
                 ("applies_fp32", ctypes.c_int), ("applies_fp64", ctypes.c_int),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("flops_update_df", ctypes.c_double)]
 
 
 class BdgError(RuntimeError):

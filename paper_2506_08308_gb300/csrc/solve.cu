@@ -354,6 +354,7 @@ class Solver {
                         double alpha = 1.0) {
     if (Q == 0) return BDG_OK;
     BDG_CUDA_TRY(plan_, update_pairs<R>(A, dC, ldc, beta, y, vlen_, Q, s_, alpha));
+    if (sizeof(R) == 8) plan_->stats.flops_update_df += 2.0 * (double)A.n * (2.0 * A.cols) * (2.0 * Q);
     return BDG_OK;
   }
   // the same with a host matrix (small data-movement matrices: diagonals, selections)
