@@ -81,3 +81,27 @@ def test_chemical_potential_rules():
     phi[1] = 0.0
     Hphi = np.stack([1.0 * phi[0], 0 * phi[1], 3.0 * phi[2]])
     assert np.allclose(spin1.chemical_potentials(phi, Hphi), [1.0, 2.0, 3.0])
+
+
+@pytest.mark.parametrize("M", [0.0, 0.25, -0.6])
+def test_project_SM_lands_on_SM(M):
+    """The scaling onto S_M: mass h^d sum |phi|^2 = 1, magnetization
+    N_1 - N_-1 = M, the scale factors obey sigma_1 sigma_-1 = sigma_0^2, a
+    point already on S_M is left unchanged, and a vanishing phi_0 stays zero
+    while N_{+-1} = (1 +- M) / 2."""
+    rng = np.random.default_rng(21)
+    cell = 0.3
+    phi = rng.uniform(0.1, 1.0, (3, 16, 12))
+    out = gs.project_SM(phi, M, cell)
+    N = cell * np.sum(out.reshape(3, -1) ** 2, axis=1)
+    assert abs(N.sum() - 1.0) < 1e-13 and abs(N[0] - N[2] - M) < 1e-13
+    sig = (out / phi).reshape(3, -1)
+    assert np.ptp(sig, axis=1).max() < 1e-13          # one factor per component
+    s1, s0, sm = sig[:, 0]
+    assert abs(s1 * sm - s0 * s0) < 1e-13 * s0 * s0
+    np.testing.assert_allclose(gs.project_SM(out, M, cell), out, rtol=1e-13, atol=0)
+    phi[1] = 0.0
+    out = gs.project_SM(phi, M, cell)
+    N = cell * np.sum(out.reshape(3, -1) ** 2, axis=1)
+    assert N[1] == 0.0
+    np.testing.assert_allclose(N[[0, 2]], [(1 + M) / 2, (1 - M) / 2], rtol=1e-13)

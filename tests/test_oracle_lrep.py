@@ -371,3 +371,55 @@ def test_pair_gram_brute_force_and_complex_identity():
     H = A.conj() @ B.T
     np.testing.assert_allclose(S[0::2, 0::2] + S[1::2, 1::2], H.real, atol=1e-13)
     np.testing.assert_allclose(S[0::2, 1::2] - S[1::2, 0::2], H.imag, atol=1e-13)
+
+
+def test_small_lrep_semidefinite_Kplus():
+    """The rank-revealing branch of small_lrep: K_+ = X diag(lam) X^T with one
+    exact zero eigenvalue and widely graded others.  The n - 1 returned
+    omega^2 are the nonzero eigenvalues of K_+ K_- (the pencil K_+ K_- q =
+    omega^2 q), K_+ p = omega q and p^T q = I hold exactly, and q lies in
+    range(K_+)."""
+    rng = np.random.default_rng(12)
+    n = 8
+    X, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.array([0.0, 1e-4, 0.3, 1.0, 2.0, 5.0, 40.0, 900.0])
+    Kp = (X * lam) @ X.T
+    Y = rng.standard_normal((n, n))
+    Km = Y @ Y.T + 0.5 * np.eye(n)
+    om, Pc, Qc = lrep.small_lrep(Kp, Km)
+    assert om.size == n - 1
+    ev = np.sort(np.linalg.eigvals(Kp @ Km).real)[1:]
+    np.testing.assert_allclose(om ** 2, ev, rtol=1e-9)
+    np.testing.assert_allclose(Kp @ Pc, Qc * om, atol=1e-9 * np.abs(Qc * om).max())
+    np.testing.assert_allclose(Pc.T @ Qc, np.eye(n - 1), atol=1e-9)
+    null = X[:, 0]
+    assert np.abs(null @ Qc).max() < 1e-9 * np.abs(Qc).max()
+
+
+def test_e_uv_closed_forms():
+    """The projector error of Section 4.1 on vectors with known angles to the
+    analytical span: zero inside the span (at any scale), one on its
+    orthogonal complement, |sin theta| for a unit vector at angle theta, and
+    the u and v parts add."""
+    rng = np.random.default_rng(13)
+    n = 60
+    U = rng.standard_normal((n, 2))
+    V = rng.standard_normal((n, 3))
+    Qu, _ = np.linalg.qr(U)
+    Qv, _ = np.linalg.qr(V)
+    u_in = U @ np.array([0.3, -1.2])
+    v_in = V @ np.array([2.0, 0.1, -0.7])
+    assert kohn.e_uv(u_in, 5.0 * v_in, U, V) < 1e-14
+    r = rng.standard_normal(n)
+    pu = r - Qu @ (Qu.T @ r)
+    pu /= np.linalg.norm(pu)
+    r = rng.standard_normal(n)
+    pv = r - Qv @ (Qv.T @ r)
+    pv /= np.linalg.norm(pv)
+    assert abs(kohn.e_uv(pu, v_in, U, V) - 1.0) < 1e-13
+    qu = Qu[:, 0]
+    qv = Qv @ (np.array([1.0, 2.0, -1.0]) / np.sqrt(6.0))
+    for a, b in ((0.1, 0.0), (0.7, 1.3), (1.5, 0.02)):
+        u = np.cos(a) * qu + np.sin(a) * pu
+        v = 3.0 * (np.cos(b) * qv + np.sin(b) * pv)
+        assert abs(kohn.e_uv(u, v, U, V) - (abs(np.sin(a)) + abs(np.sin(b)))) < 1e-13

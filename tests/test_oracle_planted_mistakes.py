@@ -259,6 +259,52 @@ def _pair_gram_parts_swapped(mp):
     mp.setattr(lrep, "pair_gram", lambda A, B: orig(1j * np.conj(A), B))
 
 
+def _kdiag_symbol_of_modulus(mp):
+    # the symbol evaluated at |mu| for |mu|^2
+    orig = disc.inverse_kdiag
+    mp.setattr(disc, "inverse_kdiag", lambda f, symbol, lo, hi: orig(f, lambda k2: symbol(np.sqrt(k2)), lo, hi))
+
+
+def _derivative_sign(mp):
+    orig = disc.spectral_derivative
+    mp.setattr(disc, "spectral_derivative", lambda f, ax, lo, hi: -orig(f, ax, lo, hi))
+
+
+def _projection_of_mass_only(mp):
+    mp.setattr(gs, "project_SM", lambda phi, M, cell: phi / np.sqrt(cell * np.sum(phi ** 2)))
+
+
+def _pencil_pseudo_inverse_scaled_wrong(mp):
+    # the pseudo-inverse L^-T built with D^-1 for D (the diagonal scaling of
+    # K_+ applied the wrong way round)
+    def small(Kp, Km, zero_tol=1e-8, rank_tol=1e-10):
+        Kp = 0.5 * (Kp + Kp.T)
+        Km = 0.5 * (Km + Km.T)
+        dd = np.sqrt(np.maximum(np.diag(Kp), 0.0))
+        d = 1.0 / dd
+        lam, Q = np.linalg.eigh((Kp * d[:, None]) * d[None, :])
+        keep = lam > rank_tol * lam.max()
+        lam, Q = lam[keep], Q[:, keep]
+        L = (Q * np.sqrt(lam)) * dd[:, None]
+        Lit = (Q / np.sqrt(lam)) * dd[:, None]
+        w2, Z = np.linalg.eigh(L.T @ Km @ L)
+        pos = w2 > zero_tol ** 2
+        om = np.sqrt(w2[pos])
+        Z = Z[:, pos]
+        s = np.sqrt(om)
+        return om, (Lit @ Z) * s, ((L @ Z) / om) * s
+    mp.setattr(lrep, "small_lrep", small)
+
+
+def _e_uv_squared(mp):
+    def euv(u_num, v_num, U_exact, V_exact):
+        def err(x, B):
+            Q, _ = np.linalg.qr(B)
+            return (np.linalg.norm(x - Q @ (Q.conj().T @ x)) / np.linalg.norm(x)) ** 2
+        return err(u_num, U_exact) + err(v_num, V_exact)
+    mp.setattr(kohn, "e_uv", euv)
+
+
 # ---------------------------------------------------------------------------
 # the cases: (name, plant, pins); a pin is (function, needs ground, args)
 # ---------------------------------------------------------------------------
@@ -315,6 +361,15 @@ CASES = [
      [(tl.test_deflation_and_iterative_solver_afm_case, G, ())]),
     ("pair Gram with real and imaginary parts swapped", _pair_gram_parts_swapped,
      [(tl.test_pair_gram_brute_force_and_complex_identity, False, ())]),
+    ("T_sigma symbol of |mu| for |mu|^2", _kdiag_symbol_of_modulus,
+     [(tdisc.test_inverse_kdiag_on_plane_waves, False, ())]),
+    ("spectral derivative with -i mu", _derivative_sign,
+     [(tdisc.test_spectral_derivative_of_sines_and_cosines, False, ()), (tl.test_kohn_mode, G, ())]),
+    ("ground state projected by mass only", _projection_of_mass_only,
+     [(tgs.test_project_SM_lands_on_SM, False, (0.25,))]),
+    ("pseudo-inverse of the K_+ factor scaled by D^-1 for D", _pencil_pseudo_inverse_scaled_wrong,
+     [(tl.test_small_lrep_semidefinite_Kplus, False, ())]),
+    ("e_uv with squared projector errors", _e_uv_squared, [(tl.test_e_uv_closed_forms, False, ())]),
 ]
 
 
