@@ -9,7 +9,9 @@ form of eqs. def_A / def_B, real ground state).
 Three independent evaluations:
   dense_matrix / apply_dense   the explicit 6P x 6P matrix (small P only);
   apply_dft                    the Laplacian by dense per-axis DFT matrices;
-  apply_fft                    the Laplacian by numpy.fft.
+  apply_fft                    the Laplacian by numpy.fft;
+and, for grids too large for those, apply_at_nodes: the product at chosen
+nodes from the grid lines through them.
 Vectors have shape (nvec, 6, P) with components (u_1, u_0, u_-1, v_1, v_0,
 v_-1) in UV form and (f_1, f_0, f_-1, g_1, g_0, g_-1) in FG form, P the number
 of nodes in C order.
@@ -122,3 +124,40 @@ def fg_to_uv(x):
     """u = f+g, v = f-g (eq. c-o-v)."""
     f, g = x[:, :3], x[:, 3:]
     return np.concatenate([f + g, f - g], axis=1)
+
+
+def apply_at_nodes(w, phi_nodes, V_nodes, mu, lines, nodes, mode=UV):
+    """The product (eq. BdG-d in UV form, eq. lrep-d in FG form) at a few nodes
+    only, for grids too large for the whole-vector evaluations.
+
+    nodes      S grid indices (n_1, ..., n_d);
+    lines[a]   (S, 6, N_a): the six fields of x on the grid line through node
+               s along axis a;
+    phi_nodes  (3, S) real ground state and V_nodes (S,) potential at the nodes.
+
+    At node s the Laplacian is the sum over the axes of row n_a of the dense
+    1-D spectral Laplacian matrix (eq. laplace_approx, a Kronecker sum on the
+    tensor grid) applied to the line along axis a; the pointwise parts are
+    the blocks of eqs. def_bfA / def_bfB at the node.  Returns (S, 6)."""
+    S = len(nodes)
+    Apt, Bpt = spin1.pointwise_blocks(np.asarray(phi_nodes).reshape(3, S), V_nodes,
+                                      w.beta_n, w.beta_s, mu, w.p, w.q)
+    Apt, Bpt = Apt.real, Bpt.real
+    lap = np.zeros((S, 6), dtype=np.complex128)
+    for a in range(len(w.n)):
+        row = disc.laplacian_matrix_1d(w.n[a], w.lo[a], w.hi[a])
+        for s in range(S):
+            lap[s] += np.asarray(lines[a][s]) @ row[nodes[s][a]]
+    x = np.stack([np.asarray(lines[0][s])[:, nodes[s][0]] for s in range(S)])
+    kin = -0.5 * lap
+    a, b = x[:, :3], x[:, 3:]
+
+    def pt(mat, v):
+        return np.einsum("sab,sb->sa", mat, v)
+    if mode == UV:
+        yu = kin[:, :3] + pt(Apt, a) + pt(Bpt, b)
+        yv = -(kin[:, 3:] + pt(Apt, b) + pt(Bpt, a))
+        return np.concatenate([yu, yv], axis=1)
+    yf = kin[:, :3] + pt(Apt + Bpt, a)
+    yg = kin[:, 3:] + pt(Apt - Bpt, b)
+    return np.concatenate([yf, yg], axis=1)

@@ -77,6 +77,73 @@ def test_apply_full_2d_block_sampled():
     plan.close()
 
 
+
+def _lines_through(grid, nodes):
+    """lines[a][s] = the (6, N_a) fields of grid (6, n_1, .., n_d) on the line
+    through node s along axis a, as complex128 host arrays."""
+    lines = []
+    for a in range(grid.dim() - 1):
+        per = []
+        for nd in nodes:
+            sl = list(nd)
+            sl[a] = slice(None)
+            per.append(grid[(slice(None),) + tuple(sl)].cpu().numpy().astype(np.complex128))
+        lines.append(np.stack(per))
+    return lines
+
+
+def test_apply_full_3d_n256_sampled():
+    """The 3-D 256^3 workload in the launch configuration the benchmark times
+    for its product: FG products of m = 32 c64 vectors and of m = 16 c128
+    vectors (3.2e9 and 1.6e9 complex entries), the blocks drawn on the
+    device.  At 40 seeded nodes (corners and the trap centre included) of
+    the first, a middle and the last vector the result is compared with the
+    oracle's product at those nodes, formed from the grid lines through
+    them: the per-node error
+    relative to |M| times the vector's RMS entry below 1e-5 (c64) and 1e-12
+    (c128), the per-entry form of the whole-vector bounds above."""
+    torch = need_torch_cuda()
+    from paper_2506_08308_gb300 import bdg
+    from oracle import apply as ap
+    w = synth.W3D_N256
+    phi = synth.initial_spinor(w)
+    phi = phi / np.sqrt(np.prod(w.h) * np.sum(phi ** 2))
+    V = synth.potential(w)
+    mu = np.array([1.0, 1.0, 1.0])
+    plan = make_plan(w, V, phi.reshape(-1), mu=mu)
+    rng = np.random.default_rng(41)
+    nodes = [(0, 0, 0), (255, 255, 255), (128, 128, 128), (128, 0, 255), (1, 254, 127)] + \
+        [tuple(int(rng.integers(0, nn)) for nn in w.n) for _ in range(35)]
+    flat = [int(np.ravel_multi_index(nd, w.n)) for nd in nodes]
+    ph = phi.reshape(3, -1)[:, flat]
+    Vn = V.reshape(-1)[flat]
+    del phi
+    # |M|: the largest kinetic symbol plus the largest pointwise row sum over
+    # the nodes, which include the trap centre (where rho, and with it the
+    # pointwise part, is largest)
+    from oracle import spin1
+    kin = 0.5 * sum((np.pi * n / (hi - lo)) ** 2 for n, lo, hi in zip(w.n, w.lo, w.hi))
+    Apt, Bpt = spin1.pointwise_blocks(ph, Vn, w.beta_n, w.beta_s, mu, w.p, w.q)
+    norm = kin + float(np.max(np.abs(Apt.real).sum(axis=2) + np.abs(Bpt.real).sum(axis=2)))
+    gen = torch.Generator(device="cuda")
+    for dt, m, tol in ((torch.complex64, w.m, 1e-5), (torch.complex128, w.m // 2, 1e-12)):
+        gen.manual_seed(w.block_seed)
+        x = torch.randn((m, 6, w.npts), dtype=dt, device="cuda", generator=gen)
+        y = plan.apply(x, bdg.FG)
+        torch.cuda.synchronize()
+        for v in (0, m // 2 + 1, m - 1):
+            xv = x[v].view((6,) + w.n)
+            yv = y[v].view((6,) + w.n)
+            rms = float(torch.linalg.vector_norm(x[v].to(torch.complex128))) / np.sqrt(6 * w.npts)
+            ref = ap.apply_at_nodes(w, ph, Vn, mu, _lines_through(xv, nodes), nodes, ap.FG)
+            got = np.stack([yv[(slice(None),) + nd].cpu().numpy() for nd in nodes])
+            err = np.abs(got - ref).max() / (norm * rms)
+            assert err < tol, (str(dt), v, err)
+        del x, y
+        torch.cuda.empty_cache()
+    plan.close()
+
+
 def test_apply_edge_cases():
     torch = need_torch_cuda()
     from paper_2506_08308_gb300 import bdg

@@ -161,3 +161,36 @@ def test_vanishing_component_rule_is_relative():
             assert abs(own0 - mu[1]) > 1e-3
         else:
             assert abs(mu[1] - own0) < 1e-12 * abs(own0)
+
+
+@pytest.mark.parametrize("w", [W1, W2, synth.Workload("t3d", (8, 6, 10), (-3.0, -2.0, -4.0), (3.0, 2.0, 4.0),
+                                                      (1.0, 1.3, 0.7), 15.0, -0.8, 0.02, 0.15)])
+def test_apply_at_nodes_matches_the_whole_product(w):
+    """The per-node product (rows of the 1-D spectral Laplacians on the grid
+    lines through a node, the pointwise blocks at the node) equals the dense
+    6P x 6P product at those nodes, both forms, corner nodes included."""
+    phi = _rand_state(w, 17)
+    V = synth.potential(w)
+    mu = np.array([0.4, 0.6, 0.5])
+    op = ap.Operator(w, phi, V, mu)
+    x = synth.random_block(w, 2, seed=8)
+    rng = np.random.default_rng(9)
+    nodes = [tuple(0 for _ in w.n), tuple(nn - 1 for nn in w.n)] + \
+        [tuple(int(rng.integers(0, nn)) for nn in w.n) for _ in range(10)]
+    flat = [int(np.ravel_multi_index(nd, w.n)) for nd in nodes]
+    ph = phi.reshape(3, -1)[:, flat]
+    Vn = V.reshape(-1)[flat]
+    for v in range(2):
+        grid = x[v].reshape((6,) + w.n)
+        lines = []
+        for a in range(w.dim):
+            per = []
+            for nd in nodes:
+                sl = list(nd)
+                sl[a] = slice(None)
+                per.append(grid[(slice(None),) + tuple(sl)])
+            lines.append(np.stack(per))
+        for mode in (ap.UV, ap.FG):
+            ref = op.apply_dense(x[v:v + 1], mode)[0][:, flat].T
+            got = ap.apply_at_nodes(w, ph, Vn, mu, lines, nodes, mode)
+            assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max(), (w.name, mode)

@@ -305,6 +305,16 @@ def _e_uv_squared(mp):
     mp.setattr(kohn, "e_uv", euv)
 
 
+def _node_product_first_axis_only(mp):
+    # the per-node Laplacian summed over the first axis only
+    orig = ap.apply_at_nodes
+
+    def at(w, phi_nodes, V_nodes, mu, lines, nodes, mode=ap.UV):
+        kept = [lines[0]] + [np.zeros_like(np.asarray(li)) for li in lines[1:]]
+        return orig(w, phi_nodes, V_nodes, mu, kept, nodes, mode)
+    mp.setattr(ap, "apply_at_nodes", at)
+
+
 # ---------------------------------------------------------------------------
 # the cases: (name, plant, pins); a pin is (function, needs ground, args)
 # ---------------------------------------------------------------------------
@@ -370,6 +380,8 @@ CASES = [
     ("pseudo-inverse of the K_+ factor scaled by D^-1 for D", _pencil_pseudo_inverse_scaled_wrong,
      [(tl.test_small_lrep_semidefinite_Kplus, False, ())]),
     ("e_uv with squared projector errors", _e_uv_squared, [(tl.test_e_uv_closed_forms, False, ())]),
+    ("per-node product with the Laplacian of the first axis only", _node_product_first_axis_only,
+     [(tmod.test_apply_at_nodes_matches_the_whole_product, False, (tmod.W2,))]),
 ]
 
 
