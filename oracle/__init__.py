@@ -13,14 +13,17 @@ Modules, each citing the passages it follows:
                   def_bfA, def_bfB), the GPE right-hand side (eq. GPE), the
                   Hamiltonian of eq. NLEP and the chemical potentials
                   (eq. chem-formula).
-  ground_state    normalized gradient flow for the ground state on S_M
-                  (eq. groundDef); the paper itself uses PCG.
+  ground_state    the ground state on S_M (eq. groundDef): normalized
+                  gradient flow, then inexact Newton steps with the Hessian
+                  H_+ (projected CG); the paper cites its PCG method without
+                  describing it.
   apply           the discrete BdG operator of eq. BdG-d / eq. lrep-d as a
-                  dense matrix, by DFT matrices, and by numpy.fft.
+                  dense matrix, by DFT matrices, by numpy.fft, and at chosen
+                  nodes from the grid lines through them (large grids).
   lrep            dense solves, the bi-orthogonal Gram-Schmidt, the
                   structure-preserving Rayleigh-Ritz step, the iterative
-                  subspace solver, residuals and the normalization of
-                  eq. constrainfg.
+                  subspace solver, residuals, the Gram of packed real
+                  columns and the normalization of eq. constrainfg.
   kohn            the analytical eigenpairs of Theorem "Analytical eigenpairs"
                   (eq. eig-pair) and the error metrics of Section 4.1.
   perturbed       the perturbed densities of single modes (Section 4.2,
@@ -29,5 +32,7 @@ Modules, each citing the passages it follows:
 Parity status: every function is pinned by a `-m "not gpu"` test against
 closed forms, invariants or library routines, except the iterates of the
 subspace solver (the paper does not give its algorithm; only its converged
-result is pinned) -- parity unpinned for the iteration history.
+result is pinned) -- parity unpinned for the iteration history.  The tests
+in tests/test_oracle_planted_mistakes.py plant plausible slips in these
+functions and check that a pin fails on each.
 """

@@ -15,6 +15,9 @@ nodes from the grid lines through them.
 Vectors have shape (nvec, 6, P) with components (u_1, u_0, u_-1, v_1, v_0,
 v_-1) in UV form and (f_1, f_0, f_-1, g_1, g_0, g_-1) in FG form, P the number
 of nodes in C order.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
+benchmark's CPU leg, never by the product library.
 """
 from __future__ import annotations
 

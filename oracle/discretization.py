@@ -8,6 +8,9 @@ DFT (eq. FT_3):   F~_k = (1/N) sum_n F(x_n) exp(-2 pi i n k / N).
 Interpolant (eq. laplace_approx): F(x_n) = sum_k F~_k W_k(x_n).
 Laplacian (eq. laplace_approx): (Lap F)(x_n) = sum_k -mu_k^2 F~_k W_k(x_n),
 the Nyquist mode k = -N/2 keeping its mu^2 (the sum runs over all k).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
+benchmark's CPU leg, never by the product library.
 """
 from __future__ import annotations
 

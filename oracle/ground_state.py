@@ -27,6 +27,9 @@ pseudospectral basis of Section 3.1:
 
 Norms carry the quadrature weight h^d (the discrete inner product of
 Section 3.3 with n = 0..N-1).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
+benchmark's CPU leg, never by the product library.
 """
 from __future__ import annotations
 

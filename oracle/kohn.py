@@ -7,6 +7,9 @@ eq. eig-pair) and the error metrics of Section 4.1.
   e_omega = |omega_N - omega| / |omega|,
   e_uv = |u_N - P_u u_N| / |u_N| + |v_N - P_v v_N| / |v_N|, P the l2
   projector onto the analytical eigenspace of that eigenvalue.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
+benchmark's CPU leg, never by the product library.
 """
 from __future__ import annotations
 

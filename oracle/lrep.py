@@ -25,6 +25,9 @@ Contents
 
 The inner products here are the unweighted Euclidean ones; the weight h^d
 enters only the normalization <f, g> = 1/4 of eq. constrainfg (reading P11).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
+benchmark's CPU leg, never by the product library.
 """
 from __future__ import annotations
 

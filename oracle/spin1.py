@@ -14,6 +14,9 @@ and their discrete forms (eqs. def_bfA, def_bfB).
 Zeeman terms: the paper has none; this oracle adds the single-particle term
 -p S_z + q S_z^2 to L (reading P1), i.e. diag(q-p, 0, q+p) on the diagonal of
 H and of A, nothing on B.  Component order is (1, 0, -1).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
+benchmark's CPU leg, never by the product library.
 """
 from __future__ import annotations
 
