@@ -797,7 +797,8 @@ class Solver {
   // ---- one solve phase ---------------------------------------------------
   // The Ritz block enters in bank U_[cur_] columns [0, nx_) with images.
   // stop_floor > 0 (FP32 phase): return once the worst of the first k
-  // residuals is below it, or after 6 iterations without a 30% gain.
+  // residuals is below it, or after fp32_stall_ iterations (1 unless
+  // BDG_FP32_STALL says otherwise) without a 30% gain.
   bdg_status iterate(int k, double tol, int maxit, double stop_floor, int* iters_out, bool* converged) {
     *converged = false;
     int nu = nx_;   // basis columns
