@@ -315,6 +315,70 @@ def _node_product_first_axis_only(mp):
     mp.setattr(ap, "apply_at_nodes", at)
 
 
+def _uv_from_fg_sign(mp):
+    # v = g - f for v = f - g
+    orig = ap.fg_to_uv
+
+    def f2u(x):
+        y = np.array(orig(x), copy=True)
+        y[:, 3:] *= -1.0
+        return y
+    mp.setattr(ap, "fg_to_uv", f2u)
+
+
+def _kronecker_order_reversed(mp):
+    def lapm(shape, lo, hi):
+        mats = [disc.laplacian_matrix_1d(nn, a, b) for nn, a, b in zip(shape, lo, hi)]
+        total = 0.0
+        for ax, mat in enumerate(mats):
+            term = np.ones((1, 1))
+            for bx in reversed(range(len(mats))):
+                term = np.kron(term, mat if bx == ax else np.eye(shape[bx]))
+            total = total + term
+        return total
+    mp.setattr(disc, "laplacian_matrix", lapm)
+
+
+def _gpe_exchange_term_dropped(mp):
+    # the beta_s phi_0^2 conj(phi_-1) term of the phi_1 equation left out
+    orig = spin1.gpe_rhs_componentwise
+
+    def rhs(psi, V, w, bn, bs, p=0.0, q=0.0):
+        r = np.array(orig(psi, V, w, bn, bs, p, q), copy=True)
+        r[0] -= bs * psi[1] ** 2 * np.conj(psi[2])
+        return r
+    mp.setattr(spin1, "gpe_rhs_componentwise", rhs)
+
+
+def _spin_vector_conjugate_side(mp):
+    # Phi^T S_j conj(Phi) for Phi^H S_j Phi
+    mp.setattr(spin1, "spin_vector",
+               lambda phi: np.stack([np.einsum("a...,ab,b...->...", phi, S, phi.conj()) for S in spin1.SPIN]))
+
+
+def _dense_g_without_omega(mp):
+    # g = L y in place of L y / omega (then normalised as usual)
+    orig = lrep.dense_solve_fg
+
+    def dense(op, k, zero_tol=1e-5):
+        om, F, G = orig(op, k, zero_tol)
+        n = len(om)
+        Fm = F.reshape(n, -1).T
+        Gm = (G * om[:, None, None]).reshape(n, -1).T
+        Fm, Gm = lrep.normalize_fg(Fm, Gm, lrep.weight(op.w))
+        return om, Fm.T.reshape(F.shape), Gm.T.reshape(G.shape)
+    mp.setattr(lrep, "dense_solve_fg", dense)
+
+
+def _g_side_never_deflated(mp):
+    orig = lrep.deflation_bases
+
+    def db(op, phi, **kw):
+        Zf, Zg = orig(op, phi, **kw)
+        return Zf, Zg[:, :0]
+    mp.setattr(lrep, "deflation_bases", db)
+
+
 # ---------------------------------------------------------------------------
 # the cases: (name, plant, pins); a pin is (function, needs ground, args)
 # ---------------------------------------------------------------------------
@@ -382,6 +446,18 @@ CASES = [
     ("e_uv with squared projector errors", _e_uv_squared, [(tl.test_e_uv_closed_forms, False, ())]),
     ("per-node product with the Laplacian of the first axis only", _node_product_first_axis_only,
      [(tmod.test_apply_at_nodes_matches_the_whole_product, False, (tmod.W2,))]),
+    ("UV from FG with v = g - f (eq. c-o-v)", _uv_from_fg_sign,
+     [(tmod.test_three_applies_agree_and_forms, False, (tmod.W1,))]),
+    ("dense Laplacian with the Kronecker factors reversed", _kronecker_order_reversed,
+     [(tdisc.test_laplacian_forms_agree_2d_3d, False, ())]),
+    ("componentwise GPE without beta_s phi_0^2 conj(phi_-1)", _gpe_exchange_term_dropped,
+     [(tmod.test_compact_equals_componentwise_gpe, False, (tmod.W1,))]),
+    ("spin vector Phi^T S conj(Phi)", _spin_vector_conjugate_side,
+     [(tmod.test_compact_equals_componentwise_gpe, False, (tmod.W2,))]),
+    ("dense route with g = L y (no 1/omega)", _dense_g_without_omega,
+     [(tl.test_biorthogonality_and_normalization, G, (tl.WFM,))]),
+    ("-i S_y Phi never deflated (reading P7)", _g_side_never_deflated,
+     [(tl.test_residuals_closed_forms_on_unconverged_pairs, G, ())]),
 ]
 
 
