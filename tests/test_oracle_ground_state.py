@@ -105,3 +105,31 @@ def test_project_SM_lands_on_SM(M):
     N = cell * np.sum(out.reshape(3, -1) ** 2, axis=1)
     assert N[1] == 0.0
     np.testing.assert_allclose(N[[0, 2]], [(1 + M) / 2, (1 - M) / 2], rtol=1e-13)
+
+
+def test_newton_step_converges_quadratically(ground):
+    """The inexact Newton step of the ground-state solver (Hessian H_+ on the
+    tangent space of S_M, solved to 1e-13): from a converged state moved by
+    delta along a smooth direction and projected back onto S_M, the residual
+    after one step falls as the square of the residual before it (the
+    observed order between delta = 1e-2 and 1e-3 is 2 within 0.1, and the
+    step gains at least a factor 100 at delta = 1e-3).  A wrong Hessian
+    converges linearly or not at all."""
+    w = synth.Workload("zq1d", (64,), (-8.0,), (8.0,), (1.0,), 10.0, -1.0, 0.0, 0.1, M=0.2, gs_seed=7)
+    V, phi, _ = ground(w)
+    V = V.reshape(w.n)
+    phi = phi.reshape((3,) + w.n)
+    cell = gs.cell_volume(w)
+    x = synth.axes(w)[0]
+    d = np.stack([np.exp(-0.3 * (x - s) ** 2) * (1 + 0.3 * np.sin(k * x))
+                  for s, k in ((0.2, 1.0), (-0.5, 2.0), (0.7, 3.0))])
+    r0s, r1s = [], []
+    for delta in (1e-2, 1e-3):
+        p0 = gs.project_SM(phi + delta * d, w.M, cell)
+        r0, _ = gs.nlep_residual(p0, V, w)
+        r1, _ = gs.nlep_residual(gs.newton_step(p0, V, w, 10.0, cell, eta=1e-13, maxcg=3000), V, w)
+        r0s.append(r0)
+        r1s.append(r1)
+    order = np.log(r1s[0] / r1s[1]) / np.log(r0s[0] / r0s[1])
+    assert abs(order - 2.0) < 0.1, (order, r0s, r1s)
+    assert r1s[1] < 1e-2 * r0s[1], (r0s, r1s)

@@ -379,6 +379,14 @@ def _g_side_never_deflated(mp):
     mp.setattr(lrep, "deflation_bases", db)
 
 
+def _newton_with_hminus(mp):
+    # the Newton step's Hessian built from H_- for H_+
+    def hess(phi, mu, V, w, d):
+        op = ap.Operator(w, phi, V, mu)
+        return op.hminus(d.reshape(1, 3, -1))[0].reshape(d.shape)
+    mp.setattr(gs, "_hplus_real", hess)
+
+
 # ---------------------------------------------------------------------------
 # the cases: (name, plant, pins); a pin is (function, needs ground, args)
 # ---------------------------------------------------------------------------
@@ -458,6 +466,8 @@ CASES = [
      [(tl.test_biorthogonality_and_normalization, G, (tl.WFM,))]),
     ("-i S_y Phi never deflated (reading P7)", _g_side_never_deflated,
      [(tl.test_residuals_closed_forms_on_unconverged_pairs, G, ())]),
+    ("ground-state Newton step with the Hessian H_-", _newton_with_hminus,
+     [(tgs.test_newton_step_converges_quadratically, G, ())]),
 ]
 
 
