@@ -13,7 +13,8 @@ Modules, each citing the passages it follows:
                   def_bfA, def_bfB), the GPE right-hand side (eq. GPE), the
                   Hamiltonian of eq. NLEP and the chemical potentials
                   (eq. chem-formula).
-  ground_state    the ground state on S_M (eq. groundDef): normalized
+  ground_state    the energy of eq. energy and the ground state on S_M
+                  (eq. groundDef): normalized
                   gradient flow, then inexact Newton steps with the Hessian
                   H_+ (projected CG); the paper cites its PCG method without
                   describing it.

@@ -62,6 +62,35 @@ def project_SM(phi: np.ndarray, M: float, cell: float) -> np.ndarray:
     return sig.reshape((3,) + (1,) * (phi.ndim - 1)) * phi
 
 
+def energy(phi, V, w) -> float:
+    """The energy of eq. energy on the grid, for a real spinor phi of shape
+    (3,)+grid: h^d sum_n [ 1/2 |grad phi_j|^2 + V |phi_j|^2 + beta_n/2 rho^2
+    + beta_s/2 |s(Phi)|^2 ], the gradient term through Parseval as
+    1/2 sum_k |mu_k|^2 |phi~_k|^2 (the interpolant's gradient, eq.
+    laplace_approx), plus the Zeeman energy sum (q - p) |phi_1|^2 +
+    (q + p) |phi_-1|^2 of reading P1.  Its derivative along a real d is
+    2 h^d <d, H Phi>, and the ground state minimises it on S_M (eq. groundDef)."""
+    phi = np.asarray(phi, dtype=np.float64)
+    d = len(w.n)
+    cell = cell_volume(w)
+    npts = int(np.prod(w.n))
+    axes = tuple(range(1, d + 1))
+    spec = np.fft.fftn(phi, axes=axes) / npts
+    k2 = np.zeros(w.n)
+    for i in range(d):
+        mu = disc.wavenumbers(w.n[i], w.lo[i], w.hi[i])
+        shape = [1] * d
+        shape[i] = w.n[i]
+        k2 = k2 + (mu ** 2).reshape(shape)
+    kinetic = 0.5 * npts * np.sum(k2[None] * np.abs(spec) ** 2)
+    rho = np.sum(phi ** 2, axis=0)
+    s = spin1.spin_vector(phi.reshape(3, -1)).real
+    z = spin1.zeeman_diag(w.p, w.q)
+    local = np.sum(np.asarray(V).reshape(w.n) * rho + 0.5 * w.beta_n * rho ** 2) + \
+        0.5 * w.beta_s * np.sum(s ** 2) + np.sum(z.reshape((3,) + (1,) * d) * phi ** 2)
+    return float(cell * (kinetic + local))
+
+
 def nonkinetic(phi, V, w):
     """N(Phi) Phi: everything of H Phi except -1/2 Lap (eq. NLEP)."""
     rho = np.sum(phi ** 2, axis=0)

@@ -133,3 +133,67 @@ def test_newton_step_converges_quadratically(ground):
     order = np.log(r1s[0] / r1s[1]) / np.log(r0s[0] / r0s[1])
     assert abs(order - 2.0) < 0.1, (order, r0s, r1s)
     assert r1s[1] < 1e-2 * r0s[1], (r0s, r1s)
+
+
+def _smooth(w, seed):
+    rng = np.random.default_rng(seed)
+    grids = np.meshgrid(*synth.axes(w), indexing="ij")
+    r2 = sum(g * g for g in grids)
+    return np.stack([np.exp(-0.2 * r2) * (0.5 + rng.uniform()) * (1 + 0.2 * np.sin(grids[0] + rng.uniform(0, 6)))
+                     for _ in range(3)])
+
+
+@pytest.mark.parametrize("w", [
+    synth.Workload("e1d", (64,), (-8.0,), (8.0,), (1.0,), 10.0, -1.5, 0.07, 0.2),
+    synth.Workload("e2d", (16, 12), (-5.0, -4.0), (5.0, 4.0), (1.0, 1.3), 20.0, 2.0, -0.03, 0.1)],
+    ids=lambda w: w.name)
+def test_energy_derivative_is_twice_the_hamiltonian(w):
+    """eq. energy and eq. NLEP: for real Phi and a real direction d,
+    dE(Phi + e d)/de at e = 0 equals 2 h^d <d, H Phi> (central differences
+    to 1e-8), the Zeeman terms of reading P1 included.  This ties the
+    energy (gradient term by Parseval) to the Hamiltonian (spectral
+    Laplacian) through two different formulas."""
+    V = synth.potential(w)
+    phi = _smooth(w, 3)
+    d = _smooth(w, 4) - _smooth(w, 5)
+    eps = 1e-5
+    fd = (gs.energy(phi + eps * d, V, w) - gs.energy(phi - eps * d, V, w)) / (2 * eps)
+    H = spin1.hamiltonian(phi, V, w, w.beta_n, w.beta_s, w.p, w.q)
+    exact = 2.0 * gs.cell_volume(w) * np.sum(d * H)
+    assert abs(fd - exact) < 1e-8 * abs(exact), (fd, exact)
+
+
+def test_gradient_flow_is_energy_diminishing():
+    """The flow phase of the ground-state solver lowers the energy of
+    eq. energy at every step (its docstring's claim; the stabiliser alpha
+    keeps the explicit factors non-negative): 40 steps from the seeded start
+    on S_M, energies non-increasing to rounding."""
+    w = synth.Workload("fl1d", (64,), (-8.0,), (8.0,), (1.0,), 30.0, -2.0, 0.0, 0.1, M=0.2, gs_seed=9)
+    V = synth.potential(w)
+    phi0 = synth.initial_spinor(w)
+    E = []
+    for k in range(0, 41, 2):
+        phi, _, _, _ = gs.ground_state(w, V, phi0, tol=0.0, maxit=k, newton_start=0.0)
+        E.append(gs.energy(phi, V, w))
+    E = np.array(E)
+    assert np.all(np.diff(E) <= 1e-13 * np.abs(E[:-1])), E
+    assert E[-1] < E[0] - 1e-3 * abs(E[0])
+
+
+def test_ground_state_minimises_the_energy_on_S_M(ground):
+    """eq. groundDef: moving the computed ground state by e d and projecting
+    back onto S_M raises the energy, and the rise is of second order in e
+    (the first-order term vanishes at a stationary point of E on S_M):
+    the observed order between e = 1e-2 and 1e-3 is 2 within 0.05."""
+    w = synth.Workload("zq1d", (64,), (-8.0,), (8.0,), (1.0,), 10.0, -1.0, 0.0, 0.1, M=0.2, gs_seed=7)
+    V, phi, _ = ground(w)
+    V = V.reshape(w.n)
+    phi = phi.reshape((3,) + w.n)
+    cell = gs.cell_volume(w)
+    E0 = gs.energy(phi, V, w)
+    for seed in (6, 7, 8):
+        d = _smooth(w, seed) - _smooth(w, seed + 10)
+        rise = [gs.energy(gs.project_SM(phi + e * d, w.M, cell), V, w) - E0 for e in (1e-2, 1e-3)]
+        assert min(rise) > 0, rise
+        order = np.log(rise[0] / rise[1]) / np.log(10.0)
+        assert abs(order - 2.0) < 0.05, (seed, rise, order)

@@ -17,6 +17,7 @@ and the readings P1, P3, P6, P7 and P9 of the paper."""
 import numpy as np
 import pytest
 
+import synth
 import test_oracle_discretization as tdisc
 import test_oracle_ground_state as tgs
 import test_oracle_lrep as tl
@@ -387,6 +388,16 @@ def _newton_with_hminus(mp):
     mp.setattr(gs, "_hplus_real", hess)
 
 
+def _energy_density_without_half(mp):
+    # beta_n rho^2 for beta_n / 2 rho^2 in eq. energy
+    orig = gs.energy
+
+    def energy(phi, V, w):
+        rho = np.sum(np.asarray(phi) ** 2, axis=0)
+        return orig(phi, V, w) + gs.cell_volume(w) * 0.5 * w.beta_n * float(np.sum(rho ** 2))
+    mp.setattr(gs, "energy", energy)
+
+
 # ---------------------------------------------------------------------------
 # the cases: (name, plant, pins); a pin is (function, needs ground, args)
 # ---------------------------------------------------------------------------
@@ -468,6 +479,9 @@ CASES = [
      [(tl.test_residuals_closed_forms_on_unconverged_pairs, G, ())]),
     ("ground-state Newton step with the Hessian H_-", _newton_with_hminus,
      [(tgs.test_newton_step_converges_quadratically, G, ())]),
+    ("energy with beta_n rho^2 for beta_n/2 rho^2 (eq. energy)", _energy_density_without_half,
+     [(tgs.test_energy_derivative_is_twice_the_hamiltonian, False, (synth.Workload(
+         "e1d", (64,), (-8.0,), (8.0,), (1.0,), 10.0, -1.5, 0.07, 0.2),))]),
 ]
 
 
